@@ -1,0 +1,212 @@
+/*
+ * sv.h -- C ABI of libsv, a GB300 (sm_103a) state-vector simulator for the
+ * data-parallel path of the JUQCS method (Willsch et al., "Benchmarking
+ * Supercomputers with the Juelich Universal Quantum Computer Simulator",
+ * arXiv:1912.03243).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * State.  An n-qubit state is 2^n complex amplitudes (Sec. 2, after Eq. 1).
+ *   Qubit j is bit j of the amplitude index (qubit 0 = least significant);
+ *   the paper leaves the order open.  Storage by dtype:
+ *     SV_C64    2^n x {float re, float im}, interleaved, 8 B per amplitude.
+ *     SV_C128   2^n x {double re, double im}, 16 B per amplitude: the exact
+ *               ("JUQCS-E") representation of Sec. 1, 2^(n+4) bytes.
+ *     SV_ENC2B  the adaptive two-byte code of Sec. 1 ("JUQCS-A"): 2^n x
+ *               {int8 re, int8 im} codes followed by 2^(n-8) float block
+ *               scales (one per 256 consecutive amplitudes; one scale when
+ *               n < 8).  Amplitude x = sign(q) * scale * fl(|q|/127).
+ *   sv_bytes_required() gives the exact device footprint of each layout.
+ * Matrices.  Complex matrices are row-major, each entry (re, im) as two
+ *   doubles.  A 2x2 gate is 8 doubles: u00 u01 u10 u11.
+ * Ownership.  Handles belong to the library until sv_free().  Every array a
+ *   caller passes (matrices, qubit lists, indices, outputs, circuit text) is
+ *   caller-owned, read or written only during the call, never retained.
+ *   A buffer given to sv_attach stays owned by the caller and must outlive
+ *   the handle.
+ * Streams.  Each handle is bound to one CUDA stream (NULL = the legacy
+ *   default stream).  Gate calls only enqueue work and return; kernel faults
+ *   surface as SV_ERR_CUDA at the next call that synchronises (sv_sync,
+ *   sv_norm, sv_amplitudes, sv_copy_to_host, sv_get_codes).
+ * Errors.  Every call returns an sv_status; nothing is thrown across the ABI.
+ *   On failure the state is unchanged when the failure is an argument
+ *   check (checked before any launch) and undefined after SV_ERR_CUDA.
+ *   sv_last_error() returns a thread-local message for the last failure.
+ * Sizes.  1 <= n <= 40 for SV_C64/SV_C128 and 1 <= n <= 40 for SV_ENC2B,
+ *   further limited by free device memory (checked before allocating).
+ * Fault injection (host side, for tests): the environment variable
+ *   SV_FAULT_INJECT=alloc|launch|sync makes the next allocation, launch or
+ *   synchronisation report SV_ERR_OOM / SV_ERR_CUDA without touching the
+ *   GPU.
+ */
+#ifndef SV_H
+#define SV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sv_state *sv_handle;
+typedef struct sv_plan_s *sv_plan;
+
+typedef enum { SV_C64 = 0, SV_C128 = 1, SV_ENC2B = 2 } sv_dtype;
+
+typedef enum {
+    SV_OK = 0,
+    SV_ERR_ARG = 1,          /* bad argument (range, repeated qubit, NULL) */
+    SV_ERR_OOM = 2,          /* not enough free device memory */
+    SV_ERR_DTYPE = 3,        /* operation not defined for this dtype */
+    SV_ERR_CUDA = 4,         /* a CUDA call or kernel failed */
+    SV_ERR_TIMEOUT = 5,      /* a bounded device-side wait gave up */
+    SV_ERR_STATE = 6,        /* handle in the wrong state (freed, busy) */
+    SV_ERR_PARSE = 7,        /* circuit text could not be parsed */
+    SV_ERR_UNSUPPORTED = 8   /* valid request outside what is implemented */
+} sv_status;
+
+/* Circuit execution modes (sv_run_circuit, sv_plan_create). */
+typedef enum {
+    SV_MODE_PERGATE = 0,     /* one HBM pass per gate (Eq. 1 per gate) */
+    SV_MODE_TILED = 1,       /* several gates per HBM pass in shared memory */
+    SV_MODE_FUSED = 2        /* tiled passes whose gates are fused into k-qubit
+                                blocks applied on the tensor cores */
+} sv_mode;
+
+/* ---- lifecycle --------------------------------------------------------- */
+
+/* Device bytes an n-qubit state of dtype dt occupies (0 if n is out of
+ * range).  SV_C128: 2^(n+4) (Sec. 1). */
+size_t sv_bytes_required(int n, sv_dtype dt);
+
+/* Allocate an n-qubit state on the current device with cudaMalloc and set it
+ * to |0...0> (Sec. 4: the machine starts in |0>).  stream: a cudaStream_t
+ * or NULL.  Errors: SV_ERR_ARG (n, dt, out), SV_ERR_OOM (checked against
+ * cudaMemGetInfo before allocating), SV_ERR_CUDA. */
+sv_status sv_alloc(int n, sv_dtype dt, void *stream, sv_handle *out);
+
+/* Wrap caller-owned device memory (e.g. a torch tensor) of at least
+ * sv_bytes_required(n, dt) bytes, 256-byte aligned.  The contents are left
+ * as they are.  Errors: SV_ERR_ARG (NULL, too small, misaligned). */
+sv_status sv_attach(int n, sv_dtype dt, void *dev_ptr, size_t bytes, void *stream, sv_handle *out);
+
+/* Synchronise and release the handle (and its memory if sv_alloc made it).
+ * NULL is accepted and ignored. */
+sv_status sv_free(sv_handle h);
+
+/* Set the state to the computational basis state |idx>.  Errors: SV_ERR_ARG
+ * (idx >= 2^n). */
+sv_status sv_set_basis(sv_handle h, uint64_t idx);
+
+/* Block until all work queued on the handle's stream is done; report any
+ * device fault. */
+sv_status sv_sync(sv_handle h);
+
+/* Thread-local message describing the last failure ("" if none). */
+const char *sv_last_error(void);
+
+/* Qubit count / dtype of a handle (-1 on a NULL handle). */
+int sv_num_qubits(sv_handle h);
+int sv_dtype_of(sv_handle h);
+
+/* ---- gates --------------------------------------------------------------- */
+
+/* Eq. 1: for every index pair (i, i + 2^target) with bit `target` clear
+ * (and bit `control` set when control >= 0), replace (a_i, a_{i+2^target})
+ * by U (a_i, a_{i+2^target}).  U: 8 doubles, 2x2 row-major.  Two-qubit
+ * controlled gates of the paper (CNOT of Sec. 3, CZ of Sec. 4) are this
+ * call with U = X or Z.  Every dtype: SV_ENC2B decodes each touched block,
+ * applies the gate in FP32 and re-encodes (Sec. 3, the "encoding-decoding
+ * operation").  Errors: SV_ERR_ARG (target/control out of range or equal,
+ * U NULL). */
+sv_status sv_apply_gate(sv_handle h, int target, int control, const double *U);
+
+/* Sec. 2: a k-qubit gate as a dense 2^k x 2^k matrix on the listed qubits
+ * (local index bit j <-> qubits[j]; qubits[0] is the least significant).
+ * 1 <= k <= 6, qubits distinct.  SV_C64 applies it on the tensor cores with
+ * split-precision BF16 products and FP32 accumulation; SV_C128 in FP64 on
+ * the CUDA cores.  Errors: SV_ERR_ARG, SV_ERR_DTYPE (SV_ENC2B). */
+sv_status sv_apply_fused(sv_handle h, int k, const int *qubits, const double *U);
+
+/* ---- circuits -------------------------------------------------------------- */
+
+/* Run a circuit given as text (one gate per line: "H 3", "CZ 0 1",
+ * "CP 2 5 0.785", "U 4 <8 doubles>", see the package documentation) on the
+ * handle's current state, with one of the sv_mode strategies.  All modes
+ * compute the same product of gate matrices (Sec. 2); they differ in how
+ * many HBM passes they make.  SV_ENC2B supports SV_MODE_PERGATE only.
+ * Errors: SV_ERR_PARSE, SV_ERR_ARG (qubit range), SV_ERR_DTYPE. */
+sv_status sv_run_circuit(sv_handle h, const char *text, int mode);
+
+/* Plan a circuit once (parse, classify gates, group them into HBM passes,
+ * upload the pass programs) and execute it many times.  The plan is bound
+ * to the handle and must be freed before it. */
+sv_status sv_plan_create(sv_handle h, const char *text, int mode, sv_plan *out);
+sv_status sv_plan_execute(sv_plan p);
+/* Statistics of a plan: number of gates, HBM passes (kernel launches) and
+ * the algorithmic bytes all passes move. */
+sv_status sv_plan_info(sv_plan p, int64_t *gates, int64_t *passes, double *bytes);
+/* Per-launch timing hook: execute the plan and record event[i] (caller-
+ * created cudaEvent_t) before launch i and event[passes] after the last. */
+sv_status sv_plan_execute_timed(sv_plan p, void *const *events, int64_t n_events);
+sv_status sv_plan_free(sv_plan p);
+
+/* ---- two-byte encoding (Sec. 1 and Sec. 3) ---------------------------------- */
+
+/* Encode an SV_C64 state into an SV_ENC2B state of the same n (blocks of 256,
+ * scale = max(|re|,|im|), q = rint(x * fl(127/scale)) clamped to +-127).
+ * Errors: SV_ERR_DTYPE, SV_ERR_ARG (n differs). */
+sv_status sv_encode2b(sv_handle src_c64, sv_handle dst_enc);
+/* Decode an SV_ENC2B state into an SV_C64 state. */
+sv_status sv_decode2b(sv_handle src_enc, sv_handle dst_c64);
+/* Copy the raw codes (2^(n+1) int8) and scales (max(1, 2^(n-8)) float) of an
+ * SV_ENC2B state to host memory (either pointer may be NULL). */
+sv_status sv_get_codes(sv_handle h, int8_t *codes, float *scales);
+
+/* ---- read-out ---------------------------------------------------------------- */
+
+/* Gather m amplitudes psi[idx[j]] into out[2j], out[2j+1] (host doubles).
+ * idx: host array of m indices < 2^n.  Synchronises. */
+sv_status sv_amplitudes(sv_handle h, size_t m, const uint64_t *idx, double *out);
+
+/* sum_i |psi_i|^2 in FP64 (partial sums of at most 8 squares in the storage
+ * precision, FP64 beyond), deterministic.  Synchronises. */
+sv_status sv_norm(sv_handle h, double *out);
+
+/* Raw copy of the whole state between device and host memory (bytes must be
+ * sv_bytes_required).  Synchronises. */
+sv_status sv_copy_to_host(sv_handle h, void *dst, size_t bytes);
+sv_status sv_copy_from_host(sv_handle h, const void *src, size_t bytes);
+
+/* ---- decomposition of entangling gates (Sec. 4) ---------------------------------- */
+
+/* Eq. 3: <z|C|0> for m bit strings z of an n-qubit circuit C (n <= 64),
+ * without the 2^n state.  Qubits in maskA form partition A, the others B.
+ * Every CZ/CP between A and B is decomposed (a CX between them is first
+ * written as H CZ H); the 2^S terms are simulated as 2^S x 2 half-size
+ * complex64 state vectors batched into one launch per pass, and the
+ * products of their coefficients are summed in FP64.  form 0: projector
+ * decomposition CP = P0 (x) 1 + P1 (x) P(theta); form 1: Eq. 2 (CZ only,
+ * weight 1/2 per decomposed gate).  z: host, out: 2m host doubles.
+ * n_cut_out (may be NULL) receives S.  stream: cudaStream_t or NULL.
+ * Errors: SV_ERR_PARSE, SV_ERR_ARG, SV_ERR_UNSUPPORTED (SWAP across the
+ * cut, CP in form 1, S > 16), SV_ERR_OOM. */
+sv_status sv_cut_amplitudes(const char *text, int n, uint64_t maskA, int form, size_t m,
+                            const uint64_t *z, double *out, int *n_cut_out, void *stream);
+
+/* ---- host-only helpers (no GPU needed) -------------------------------------------- */
+
+/* The library's own matrix for a named gate of the circuit format: writes 8
+ * doubles (1-qubit) or 32 doubles (2-qubit, local index = bit(first) +
+ * 2 bit(second)); returns 1 or 2 qubits, or -1 if the name is unknown. */
+int sv_gate_matrix(const char *name, const double *params, int n_params, double *out);
+
+/* Library version string. */
+const char *sv_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SV_H */

@@ -1,0 +1,28 @@
+// Circuit plans: the host-side planner output that sv_plan_execute replays.
+#pragma once
+
+#include <vector>
+
+#include "sv_internal.h"
+
+namespace sv {
+
+constexpr int kMaxFusedQubits = 6;
+
+// Dense k-qubit block (sv_apply_fused); U is 2^k x 2^k complex row-major on
+// the host, copied into handle scratch before the launch.
+cudaError_t launch_fused(sv_state *h, int k, const int *qubits, const double *U);
+
+// Algorithmic HBM bytes of one per-gate update (what the method must move:
+// read + write of every amplitude the update changes).
+double gate1_bytes(const sv_state *h, const Gate1 &g);
+
+}  // namespace sv
+
+struct sv_plan_s {
+    sv_state *h = nullptr;
+    int mode = 0;
+    int64_t gates = 0;                 // gates of the circuit text
+    std::vector<sv::Gate1> pergate;    // SV_MODE_PERGATE
+    double bytes = 0.0;                // algorithmic bytes of one execution
+};

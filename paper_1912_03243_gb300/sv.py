@@ -1,0 +1,267 @@
+"""Thin ctypes binding of libsv (include/sv.h).
+
+Argument marshalling only: every step of the simulation runs in the CUDA
+library.  The module-level functions carry the C names; ``StateVector`` wraps
+a handle whose storage is a torch CUDA tensor attached with ``sv_attach`` and
+whose stream is torch's current stream.  There is no CPU fallback: if
+``libsv.so`` is missing or fails to load, every call raises.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsv.so")
+
+SV_C64, SV_C128, SV_ENC2B = 0, 1, 2
+DTYPES = {"c64": SV_C64, "c128": SV_C128, "enc2b": SV_ENC2B}
+SV_MODE_PERGATE, SV_MODE_TILED, SV_MODE_FUSED = 0, 1, 2
+MODES = {"pergate": SV_MODE_PERGATE, "tiled": SV_MODE_TILED, "fused": SV_MODE_FUSED}
+
+STATUS = {0: "SV_OK", 1: "SV_ERR_ARG", 2: "SV_ERR_OOM", 3: "SV_ERR_DTYPE", 4: "SV_ERR_CUDA",
+          5: "SV_ERR_TIMEOUT", 6: "SV_ERR_STATE", 7: "SV_ERR_PARSE", 8: "SV_ERR_UNSUPPORTED"}
+
+# every symbol include/sv.h declares, with (restype, argtypes)
+_vp = ctypes.c_void_p
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+_u64p = ctypes.POINTER(ctypes.c_uint64)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+_st = ctypes.c_int
+SIGNATURES = {
+    "sv_bytes_required": (ctypes.c_size_t, [ctypes.c_int, ctypes.c_int]),
+    "sv_alloc": (_st, [ctypes.c_int, ctypes.c_int, _vp, ctypes.POINTER(_vp)]),
+    "sv_attach": (_st, [ctypes.c_int, ctypes.c_int, _vp, ctypes.c_size_t, _vp, ctypes.POINTER(_vp)]),
+    "sv_free": (_st, [_vp]),
+    "sv_set_basis": (_st, [_vp, ctypes.c_uint64]),
+    "sv_sync": (_st, [_vp]),
+    "sv_last_error": (ctypes.c_char_p, []),
+    "sv_num_qubits": (ctypes.c_int, [_vp]),
+    "sv_dtype_of": (ctypes.c_int, [_vp]),
+    "sv_apply_gate": (_st, [_vp, ctypes.c_int, ctypes.c_int, _dp]),
+    "sv_apply_fused": (_st, [_vp, ctypes.c_int, _ip, _dp]),
+    "sv_run_circuit": (_st, [_vp, ctypes.c_char_p, ctypes.c_int]),
+    "sv_plan_create": (_st, [_vp, ctypes.c_char_p, ctypes.c_int, ctypes.POINTER(_vp)]),
+    "sv_plan_execute": (_st, [_vp]),
+    "sv_plan_info": (_st, [_vp, _i64p, _i64p, _dp]),
+    "sv_plan_execute_timed": (_st, [_vp, ctypes.POINTER(_vp), ctypes.c_int64]),
+    "sv_plan_free": (_st, [_vp]),
+    "sv_encode2b": (_st, [_vp, _vp]),
+    "sv_decode2b": (_st, [_vp, _vp]),
+    "sv_get_codes": (_st, [_vp, ctypes.POINTER(ctypes.c_int8), ctypes.POINTER(ctypes.c_float)]),
+    "sv_amplitudes": (_st, [_vp, ctypes.c_size_t, _u64p, _dp]),
+    "sv_norm": (_st, [_vp, _dp]),
+    "sv_copy_to_host": (_st, [_vp, _vp, ctypes.c_size_t]),
+    "sv_copy_from_host": (_st, [_vp, _vp, ctypes.c_size_t]),
+    "sv_cut_amplitudes": (_st, [ctypes.c_char_p, ctypes.c_int, ctypes.c_uint64, ctypes.c_int, ctypes.c_size_t,
+                                _u64p, _dp, _ip, _vp]),
+    "sv_gate_matrix": (ctypes.c_int, [ctypes.c_char_p, _dp, ctypes.c_int, _dp]),
+    "sv_version": (ctypes.c_char_p, []),
+}
+
+_lib = None
+_lock = threading.Lock()
+
+
+class SVError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: {STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def lib() -> ctypes.CDLL:
+    """Load libsv.so (built by paper_1912_03243_gb300.build); raise if absent."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"libsv.so not built ({LIB_PATH}); run paper_1912_03243_gb300.build.build()")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(status: int, where: str) -> None:
+    if status != 0:
+        raise SVError(status, where, lib().sv_last_error().decode())
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(_dp)
+
+
+def _text(circuit) -> bytes:
+    return (circuit if isinstance(circuit, str) else circuit.text()).encode()
+
+
+# ---- module-level functions with the C names --------------------------------
+
+def sv_bytes_required(n: int, dtype: str | int = "c64") -> int:
+    return int(lib().sv_bytes_required(n, DTYPES.get(dtype, dtype)))
+
+
+def sv_gate_matrix(name: str, params=()) -> np.ndarray:
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    out = np.zeros(32, dtype=np.float64)
+    k = lib().sv_gate_matrix(name.encode(), _dptr(p) if p.size else None, int(p.size), _dptr(out))
+    if k < 0:
+        raise ValueError(f"unknown gate {name}")
+    d = 2 if k == 1 else 4
+    return out[: 2 * d * d].view(np.complex128).reshape(d, d).copy()
+
+
+def sv_cut_amplitudes(circuit, n: int, mask_a: int, z, form: int = 0, stream=None):
+    """Eq. 3 branch sum on the GPU; returns (amplitudes complex128[m], S)."""
+    import torch
+
+    zz = np.ascontiguousarray(z, dtype=np.uint64)
+    out = np.zeros(2 * zz.size, dtype=np.float64)
+    s = ctypes.c_int(0)
+    st = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+    _check(lib().sv_cut_amplitudes(_text(circuit), n, ctypes.c_uint64(mask_a), form, zz.size,
+                                   zz.ctypes.data_as(_u64p), _dptr(out), ctypes.byref(s), _vp(st)),
+           "sv_cut_amplitudes")
+    return out.view(np.complex128).copy(), s.value
+
+
+class Plan:
+    """A planned circuit (sv_plan_create); execute() replays it."""
+
+    def __init__(self, state: "StateVector", circuit, mode: str | int = "pergate"):
+        self.state = state
+        self.handle = _vp()
+        _check(lib().sv_plan_create(state.handle, _text(circuit), MODES.get(mode, mode), ctypes.byref(self.handle)),
+               "sv_plan_create")
+        g, p, b = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_double()
+        _check(lib().sv_plan_info(self.handle, ctypes.byref(g), ctypes.byref(p), ctypes.byref(b)), "sv_plan_info")
+        self.gates, self.passes, self.bytes = g.value, p.value, b.value
+
+    def execute(self) -> None:
+        _check(lib().sv_plan_execute(self.handle), "sv_plan_execute")
+
+    def execute_timed(self, events) -> None:
+        """events: list of torch.cuda.Event (passes + 1), recorded around each launch."""
+        arr = (_vp * len(events))(*[_vp(e.cuda_event) for e in events])
+        _check(lib().sv_plan_execute_timed(self.handle, arr, len(events)), "sv_plan_execute_timed")
+
+    def free(self) -> None:
+        if self.handle:
+            _check(lib().sv_plan_free(self.handle), "sv_plan_free")
+            self.handle = _vp()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class StateVector:
+    """An n-qubit state in device memory owned by a torch tensor."""
+
+    def __init__(self, n: int, dtype: str = "c64", device=None, stream=None):
+        import torch
+
+        self.n = n
+        self.dtype = dtype
+        self.dt = DTYPES[dtype]
+        nbytes = sv_bytes_required(n, self.dt)
+        if nbytes == 0:
+            raise ValueError(f"bad qubit count {n}")
+        dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.buffer = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
+        self.handle = _vp()
+        _check(lib().sv_attach(n, self.dt, _vp(self.buffer.data_ptr()), nbytes, _vp(self.stream.cuda_stream),
+                               ctypes.byref(self.handle)), "sv_attach")
+        self.set_basis(0)
+
+    # lifecycle
+    def free(self) -> None:
+        if self.handle:
+            _check(lib().sv_free(self.handle), "sv_free")
+            self.handle = _vp()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def set_basis(self, idx: int = 0) -> None:
+        _check(lib().sv_set_basis(self.handle, idx), "sv_set_basis")
+
+    def sync(self) -> None:
+        _check(lib().sv_sync(self.handle), "sv_sync")
+
+    # gates
+    def apply_gate(self, target: int, u, control: int = -1) -> None:
+        m = np.ascontiguousarray(u, dtype=np.complex128).reshape(4)
+        _check(lib().sv_apply_gate(self.handle, target, control, _dptr(m.view(np.float64))), "sv_apply_gate")
+
+    def apply_fused(self, qubits, u) -> None:
+        qs = np.ascontiguousarray(qubits, dtype=np.int32)
+        m = np.ascontiguousarray(u, dtype=np.complex128).reshape(-1)
+        _check(lib().sv_apply_fused(self.handle, len(qs), qs.ctypes.data_as(_ip), _dptr(m.view(np.float64))),
+               "sv_apply_fused")
+
+    def run(self, circuit, mode: str | int = "pergate") -> None:
+        _check(lib().sv_run_circuit(self.handle, _text(circuit), MODES.get(mode, mode)), "sv_run_circuit")
+
+    def plan(self, circuit, mode: str | int = "pergate") -> Plan:
+        return Plan(self, circuit, mode)
+
+    # codec
+    def encode_from(self, src: "StateVector") -> None:
+        _check(lib().sv_encode2b(src.handle, self.handle), "sv_encode2b")
+
+    def decode_to(self, dst: "StateVector") -> None:
+        _check(lib().sv_decode2b(self.handle, dst.handle), "sv_decode2b")
+
+    def codes(self):
+        nb = max(1, (1 << self.n) >> 8)
+        codes = np.zeros(2 << self.n, dtype=np.int8)
+        scales = np.zeros(nb, dtype=np.float32)
+        _check(lib().sv_get_codes(self.handle, codes.ctypes.data_as(ctypes.POINTER(ctypes.c_int8)),
+                                  scales.ctypes.data_as(ctypes.POINTER(ctypes.c_float))), "sv_get_codes")
+        return codes, scales
+
+    # read-out
+    def amplitudes(self, idx) -> np.ndarray:
+        ii = np.ascontiguousarray(idx, dtype=np.uint64)
+        out = np.zeros(2 * ii.size, dtype=np.float64)
+        _check(lib().sv_amplitudes(self.handle, ii.size, ii.ctypes.data_as(_u64p), _dptr(out)), "sv_amplitudes")
+        return out.view(np.complex128).copy()
+
+    def norm(self) -> float:
+        out = ctypes.c_double()
+        _check(lib().sv_norm(self.handle, ctypes.byref(out)), "sv_norm")
+        return out.value
+
+    def to_numpy(self) -> np.ndarray:
+        """Whole state to host (complex64/complex128; raw bytes for enc2b)."""
+        nbytes = sv_bytes_required(self.n, self.dt)
+        raw = np.empty(nbytes, dtype=np.uint8)
+        _check(lib().sv_copy_to_host(self.handle, raw.ctypes.data_as(_vp), nbytes), "sv_copy_to_host")
+        if self.dt == SV_C64:
+            return raw.view(np.complex64)
+        if self.dt == SV_C128:
+            return raw.view(np.complex128)
+        return raw
+
+    def from_numpy(self, psi: np.ndarray) -> None:
+        want = {SV_C64: np.complex64, SV_C128: np.complex128}.get(self.dt)
+        arr = np.ascontiguousarray(psi, dtype=want) if want else np.ascontiguousarray(psi, dtype=np.uint8)
+        nbytes = sv_bytes_required(self.n, self.dt)
+        if arr.nbytes != nbytes:
+            raise ValueError(f"need {nbytes} bytes, got {arr.nbytes}")
+        _check(lib().sv_copy_from_host(self.handle, arr.ctypes.data_as(_vp), nbytes), "sv_copy_from_host")

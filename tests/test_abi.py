@@ -1,0 +1,88 @@
+"""The C-ABI library without a GPU: it builds, loads, exports every symbol
+include/sv.h declares, and answers host-only calls and argument errors."""
+
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1912_03243_gb300 import build as B
+from paper_1912_03243_gb300 import circuits as C
+from paper_1912_03243_gb300 import sv
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "sv.h")
+
+
+@pytest.fixture(scope="module")
+def L():
+    B.build()
+    return sv.lib()
+
+
+def declared_symbols():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(sv_\w+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(L):
+    names = declared_symbols()
+    assert len(names) >= 20
+    for name in names:
+        assert hasattr(L, name), name
+    # and the binding knows the same set
+    assert set(names) == set(sv.SIGNATURES), set(names) ^ set(sv.SIGNATURES)
+
+
+def test_bytes_required(L):
+    assert sv.sv_bytes_required(20, "c64") == 8 << 20
+    assert sv.sv_bytes_required(30, "c128") == 2 ** (30 + 4)  # Sec. 1: 2^(N+4) bytes
+    assert sv.sv_bytes_required(35, "enc2b") == 2 * 2 ** 35 + 4 * 2 ** 27  # 64 GB + 512 MB
+    assert sv.sv_bytes_required(5, "enc2b") == 64 + 4
+    assert sv.sv_bytes_required(0, "c64") == 0
+    assert sv.sv_bytes_required(41, "c64") == 0
+
+
+def test_gate_tables_agree(L, orc):
+    """Both sides hard-code the gate table independently; they must agree."""
+    for name in C.ONE_QUBIT:
+        assert np.array_equal(sv.sv_gate_matrix(name), orc.gate_matrix(name)), name
+    for name, ps in (("P", [0.37]), ("CP", [-1.1]), ("CZ", []), ("CX", []), ("SWAP", [])):
+        assert np.allclose(sv.sv_gate_matrix(name, ps), orc.gate_matrix(name, ps), atol=0, rtol=0), name
+    u = [0.6, 0.0, 0.0, 0.8, 0.0, 0.8, 0.6, 0.0]
+    assert np.array_equal(sv.sv_gate_matrix("U", u), orc.gate_matrix("U", u))
+    with pytest.raises(ValueError):
+        sv.sv_gate_matrix("NOPE")
+
+
+def test_argument_errors_without_gpu(L):
+    h = ctypes.c_void_p()
+    assert L.sv_alloc(0, 0, None, ctypes.byref(h)) == 1          # SV_ERR_ARG
+    assert L.sv_alloc(20, 7, None, ctypes.byref(h)) == 1
+    assert L.sv_alloc(20, 0, None, None) == 1
+    u = (ctypes.c_double * 8)()
+    assert L.sv_apply_gate(None, 0, -1, u) == 1
+    assert L.sv_norm(None, None) == 1
+    assert L.sv_free(None) == 0
+    assert L.sv_attach(10, 0, None, 0, None, ctypes.byref(h)) == 1
+    assert b"NULL" in L.sv_last_error()
+    assert L.sv_version().startswith(b"libsv")
+
+
+def test_fault_injection_alloc(L, monkeypatch):
+    """SV_FAULT_INJECT=alloc reports SV_ERR_OOM before touching the GPU."""
+    monkeypatch.setenv("SV_FAULT_INJECT", "alloc")
+    h = ctypes.c_void_p()
+    assert L.sv_alloc(10, 0, None, ctypes.byref(h)) == 2
+    assert b"injected" in L.sv_last_error()
+    assert not h.value
+
+
+def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
+    """No CPU fallback: a missing libsv.so is an error, not a silent path."""
+    monkeypatch.setattr(sv, "_lib", None)
+    monkeypatch.setattr(sv, "LIB_PATH", str(tmp_path / "missing.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        sv.lib()
