@@ -1,0 +1,420 @@
+#!/usr/bin/env python
+"""Benchmark: gates/s and HBM GB/s at 32 qubits, fused vs per-gate.
+
+Workload: the random circuit family at 32 qubits, depth 24, seed 1 (1140
+gates: {H,T,SX,SY} on every qubit per layer, then CZ on alternating
+neighbour pairs), complex64 state of 2^32 amplitudes (32 GiB) starting from
+|0...0>.  One step = reset to |0...0> plus the whole circuit.  The state is
+larger than L2, so no flush is needed between steps.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle
+instead (the reference arm of this project), on a bounded sample of the same
+workload.  Multi-GPU runs are independent replicas (the state-vector path
+does not shard without an exchange step); value = all ranks' gates / max time.
+"""
+
+from __future__ import annotations
+
+import argparse
+import glob
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "gates/s & HBM GB/s at 32 qubits: fused vs per-gate, err <=1e-5 vs FP64"
+HBM_FALLBACK = 6800.0
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--mode", default="auto", choices=["auto", "pergate", "tiled", "fused"])
+    ap.add_argument("--n", type=int, default=32)
+    ap.add_argument("--depth", type=int, default=24)
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--compare-steps", type=int, default=1, help="steps of the per-gate path timed for comparison")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl" if args.impl == "ours" else "gloo")
+    if args.impl == "ours":
+        torch.cuda.set_device(local)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(world, value: float) -> float:
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def workload(args):
+    from paper_1912_03243_gb300 import circuits as C
+
+    circ = C.random_circuit(args.n, args.depth, args.seed)
+    desc = (f"random circuit, {args.n} qubits, depth {args.depth}, seed {args.seed} "
+            f"({len(circ)} gates: {{H,T,SX,SY}} per qubit per layer + alternating CZ), complex64 from |0...0>")
+    return circ, desc
+
+
+# ----------------------------------------------------------------- CPU oracle
+
+def oracle_sample(args, budget_s: float, min_s: float = 10.0):
+    """Time the CPU oracle (single thread, complex128) on successive layers of
+    the same circuit family at a smaller qubit count; gates/s is scaled to
+    args.n by 2^(n_sample - n) (the oracle's cost per gate is proportional to
+    2^n).  Returns (gates/s at args.n, description, seconds)."""
+    import oracle
+    from paper_1912_03243_gb300 import circuits as C
+
+    ns = min(args.n, 26)
+    full = C.random_circuit(ns, args.depth, args.seed)
+    # split into layers: ns single-qubit gates followed by that layer's CZs
+    gates, per_layer, i = full.gates, [], 0
+    for _ in range(args.depth):
+        start = i
+        i += ns
+        while i < len(gates) and gates[i][0] == "CZ":
+            i += 1
+        c = C.Circuit(ns)
+        c.gates = gates[start:i]
+        per_layer.append(c)
+    psi = oracle.basis_state(ns)
+    done, t_used = 0, 0.0
+    for c in per_layer:
+        t0 = time.perf_counter()
+        psi = oracle.run(c, psi=psi)
+        t_used += time.perf_counter() - t0
+        done += len(c)
+        if t_used >= min_s or t_used >= budget_s:
+            break
+    gps_sample = done / t_used
+    scaled = gps_sample * 2.0 ** (ns - args.n)
+    desc = (f"oracle (plain C, complex128, 1 thread) on the first {done} gates of the same circuit family at "
+            f"{ns} qubits ({(16 << ns) >> 20} MiB): {gps_sample:.2f} gates/s, scaled by 2^({ns}-{args.n}) to "
+            f"{args.n} qubits")
+    return scaled, desc, t_used
+
+
+def run_reference(args, world, rank):
+    """The reference arm: the CPU oracle as it stands, on host cores."""
+    if rank != 0:
+        return
+    per_step = []
+    desc = None
+    for k in range(args.warmup + args.steps):
+        v, desc, t = oracle_sample(args, budget_s=8.0, min_s=2.0)
+        if k >= args.warmup:
+            per_step.append((v, t))
+    value = statistics.median([v for v, _ in per_step])
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "gates/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median([t for _, t in per_step]),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload(args)[1], "n": args.n, "depth": args.depth},
+        "cpu_baseline": {"value": value, "unit": "gates/s", "cores": 1, "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": "gates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------- ncu traffic
+
+def traffic_from_profiles(kernel: str, n: int):
+    """DRAM bytes per launch from a committed ncu summary: a summary file under
+    profiles/ carries lines 'kernel: <name>', 'dram_bytes_per_amplitude: <x>'
+    and 'source_sha1: <sha1 of the kernel's .cu at capture>'; stale summaries
+    (source changed since) give None."""
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        kv = {}
+        with open(path) as f:
+            for line in f:
+                if ":" in line and not line.startswith("#"):
+                    k, v = line.split(":", 1)
+                    kv[k.strip().strip("-* `")] = v.strip().strip("`")
+        if kv.get("kernel") != kernel or "dram_bytes_per_amplitude" not in kv:
+            continue
+        src = os.path.join(ROOT, "paper_1912_03243_gb300", "csrc", kv.get("source", ""))
+        if not os.path.exists(src):
+            continue
+        with open(src, "rb") as f:
+            if hashlib.sha1(f.read()).hexdigest() != kv.get("source_sha1"):
+                return None, path
+        return float(kv["dram_bytes_per_amplitude"]) * (1 << n), path
+    return None, None
+
+
+# ----------------------------------------------------------------- GPU arm
+
+def time_plan(S, state, plan, steps, warmup, world, with_events=True):
+    """Returns (max-over-ranks seconds for `steps` steps, per-launch durations in ms)."""
+    import torch
+
+    stream = state.stream
+    for _ in range(warmup):
+        state.set_basis(0)
+        plan.execute()
+    torch.cuda.synchronize()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(plan.passes + 1)] for _ in range(steps)]
+    if with_events:
+        # torch creates the CUDA event on its first record(); do that before
+        # handing the handles to the library
+        for row in ev:
+            for e in row:
+                e.record(stream)
+        torch.cuda.synchronize()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        start.record(stream)
+        for k in range(steps):
+            state.set_basis(0)
+            if with_events:
+                plan.execute_timed(ev[k])
+            else:
+                plan.execute()
+        end.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    t = start.elapsed_time(end) / 1e3
+    per_launch = []
+    if with_events:
+        for k in range(steps):
+            per_launch.append([ev[k][i].elapsed_time(ev[k][i + 1]) for i in range(plan.passes)])
+    return max_over_ranks(world, t), per_launch
+
+
+def best_mode(S, state, circ):
+    for mode in ("fused", "tiled", "pergate"):
+        try:
+            p = state.plan(circ, mode)
+            return mode, p
+        except S.SVError:
+            continue
+    raise RuntimeError("no execution mode available")
+
+
+def run_ours(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    from paper_1912_03243_gb300 import build as B
+    from paper_1912_03243_gb300 import circuits as C
+    from paper_1912_03243_gb300 import sv as S
+
+    if not os.path.exists(S.LIB_PATH):
+        B.build()
+    S.lib()
+    circ, desc = workload(args)
+    state = S.StateVector(args.n, "c64")
+    if args.mode == "auto":
+        mode, plan = best_mode(S, state, circ)
+    else:
+        mode, plan = args.mode, state.plan(circ, args.mode)
+    info = plan.launch_info()
+    hbm_peak, peak_kind = peaks()
+
+    with ClockSampler(local) as clk:
+        t, per_launch = time_plan(S, state, plan, args.steps, args.warmup, world)
+    clocks = clk.summary()
+    gates = plan.gates
+    value = gates * args.steps * world / t
+    ms_per_step = 1e3 * t / args.steps
+    gbs = plan.bytes * args.steps * world / t / 1e9
+
+    # dominant kernel: largest total device time over the timed steps
+    tot, cnt, byt = {}, {}, {}
+    for k in range(args.steps):
+        for i, (name, b) in enumerate(info):
+            tot[name] = tot.get(name, 0.0) + per_launch[k][i]
+            cnt[name] = cnt.get(name, 0) + 1
+            byt[name] = byt.get(name, 0.0) + b
+    dom = max(tot, key=tot.get)
+    achieved = byt[dom] / (tot[dom] / 1e3) / 1e9
+    traffic, tsrc = traffic_from_profiles(dom.split("<")[0], args.n)
+    launches_per_step = len(info)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+                "traffic": traffic,
+                "kernel": dom, "launches": cnt[dom], "avg_launch_ms": tot[dom] / cnt[dom],
+                "bytes_per_launch": byt[dom] / cnt[dom], "peak_kind": peak_kind,
+                "frac_of_nominal_8tbs": achieved / 8000.0,
+                "share_of_step": tot[dom] / sum(tot.values())}
+
+    # accuracy: the circuit followed by its inverse returns |0...0>
+    inv = state.plan(C.inverse_circuit(circ), mode)
+    state.set_basis(0)
+    plan.execute()
+    inv.execute()
+    a0 = state.amplitudes([0])[0]
+    roundtrip_infidelity = 1.0 - abs(a0) ** 2
+    inv.free()
+
+    # comparison: the plain per-gate path on the same workload
+    compare = None
+    if mode != "pergate" and args.compare_steps > 0:
+        pg = state.plan(circ, "pergate")
+        tp, _ = time_plan(S, state, pg, args.compare_steps, 1, world, with_events=False)
+        compare = {"mode": "pergate", "gates_per_s": pg.gates * args.compare_steps * world / tp,
+                   "gbs": pg.bytes * args.compare_steps * world / tp / 1e9, "launches_per_step": pg.passes,
+                   "ms_per_step": 1e3 * tp / args.compare_steps,
+                   "layers_per_s": args.depth * args.compare_steps * world / tp}
+        pg.free()
+
+    # end to end through the C ABI with host buffers: circuit text in, 1024
+    # amplitudes out, parse + plan + upload + run + read-back every step
+    e2e = None
+    if not args.no_e2e:
+        idx = C.random_bitstrings(1024, args.n, 7)
+        text = circ.text()
+        torch.cuda.synchronize()
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            state.set_basis(0)
+            state.run(text, mode)
+            amps = state.amplitudes(idx)
+        torch.cuda.synchronize()
+        te = max_over_ranks(world, time.perf_counter() - t0)
+        e2e = {"value": gates * args.steps * world / te, "unit": "gates/s",
+               "h2d_bytes_per_step": len(text.encode()) + idx.nbytes, "d2h_bytes_per_step": amps.nbytes,
+               "ms_per_step": 1e3 * te / args.steps}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, sdesc, tcpu = oracle_sample(args, budget_s=30.0)
+        cpu = {"value": v, "unit": "gates/s", "cores": 1, "kind": "oracle", "sample": sdesc}
+
+    plan.free()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "gates/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": desc, "n": args.n, "depth": args.depth, "seed": args.seed, "state": "complex64",
+                       "mode": mode, "launches_per_step": launches_per_step, "parallelism": f"replicas x{world}",
+                       "l2": "state (32 GiB) larger than L2, no flush"},
+            "hbm_gbs": gbs, "layers_per_s": args.depth * args.steps * world / t,
+            "accuracy": {"roundtrip_1_minus_fidelity": roundtrip_infidelity},
+            "compare": compare, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "gpu_launches": args.steps * (launches_per_step + 1),
+        }
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -151,6 +151,9 @@ sv_status sv_plan_info(sv_plan p, int64_t *gates, int64_t *passes, double *bytes
  * created cudaEvent_t) before launch i and event[passes] after the last. */
 sv_status sv_plan_execute_timed(sv_plan p, void *const *events, int64_t n_events);
 sv_status sv_plan_free(sv_plan p);
+/* Launch i of a plan (0 <= i < passes): the name of the kernel it runs and
+ * the algorithmic bytes it moves.  *kernel points to a static string. */
+sv_status sv_plan_launch_info(sv_plan p, int64_t i, const char **kernel, double *bytes);
 
 /* ---- two-byte encoding (Sec. 1 and Sec. 3) ---------------------------------- */
 

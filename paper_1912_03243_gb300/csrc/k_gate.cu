@@ -354,6 +354,16 @@ __global__ void k_gather(const C2<R> *__restrict__ psi, const uint64_t *__restri
 
 int norm_partials_needed(const sv_state *) { return kNormBlocks; }
 
+const char *gate1_kernel_name(const sv_state *h, const Gate1 &g) {
+    if (h->dt == SV_ENC2B) return g.target < kEncBlockLog2 || h->n < kEncBlockLog2 ? "k_enc_gate_in" : "k_enc_gate_across";
+    const bool diag = g.u[1].re == 0 && g.u[1].im == 0 && g.u[2].re == 0 && g.u[2].im == 0;
+    const bool unit00 = g.u[0].re == 1 && g.u[0].im == 0;
+    const bool c64 = h->dt == SV_C64;
+    if (diag && unit00) return c64 ? "k_phase<f32>" : "k_phase<f64>";
+    if (c64 && g.target == 0) return "k_gate_inner<f32>";
+    return c64 ? "k_gate_across<f32>" : "k_gate_across<f64>";
+}
+
 cudaError_t launch_gate1(sv_state *h, const Gate1 &g) {
     if (h->dt == SV_C64) return gate1_impl<float>(h, g);
     if (h->dt == SV_C128) return gate1_impl<double>(h, g);

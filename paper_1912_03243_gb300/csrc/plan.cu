@@ -18,6 +18,53 @@ double gate1_bytes(const sv_state *h, const Gate1 &g) {
     return 2.0 * amps * s * frac;
 }
 
+namespace {
+
+void destroy_plan(sv_plan_s *p) {
+    if (p->d_ops) cudaFree(p->d_ops);
+    if (p->d_segs) cudaFree(p->d_segs);
+    delete p;
+}
+
+template <typename R>
+sv_status upload_tile_plan(sv_plan_s *p, const TilePlan<R> &tp) {
+    p->tpasses = tp.passes;
+    const size_t ob = tp.ops.size() * sizeof(TileOp<R>), sb = tp.segs.size() * sizeof(TileSeg);
+    SV_CUDA_TRY(cudaMalloc(&p->d_ops, ob > 0 ? ob : 16));
+    SV_CUDA_TRY(cudaMalloc(&p->d_segs, sb > 0 ? sb : 16));
+    if (ob) SV_CUDA_TRY(cudaMemcpy(p->d_ops, tp.ops.data(), ob, cudaMemcpyHostToDevice));
+    if (sb) SV_CUDA_TRY(cudaMemcpy(p->d_segs, tp.segs.data(), sb, cudaMemcpyHostToDevice));
+    const double pass_bytes = 2.0 * double(uint64_t(1) << p->h->n) * (p->h->dt == SV_C64 ? 8.0 : 16.0);
+    for (size_t i = 0; i < tp.passes.size(); ++i) {
+        p->launches.push_back(PlanLaunch{1, int(i), pass_bytes});
+        p->bytes += pass_bytes;
+    }
+    return SV_OK;
+}
+
+sv_status build_tile_plan(sv_state *h, const Circuit &c, sv_plan_s *p) {
+    if (h->dt == SV_C64) {
+        TilePlan<float> tp;
+        sv_status s = plan_tiles<float>(c, h->n, TileConfig{kTileM64, kTileRB64, kTileLow64, true}, &tp);
+        return s ? s : upload_tile_plan(p, tp);
+    }
+    TilePlan<double> tp;
+    sv_status s = plan_tiles<double>(c, h->n, TileConfig{kTileM128, kTileRB128, kTileLow128, false}, &tp);
+    return s ? s : upload_tile_plan(p, tp);
+}
+
+cudaError_t launch_one(sv_plan_s *p, const PlanLaunch &l) {
+    if (l.kind == 0) return launch_gate1(p->h, p->pergate[size_t(l.index)]);
+    return launch_tile_pass(p->h, p->tpasses[size_t(l.index)], p->d_ops, p->d_segs);
+}
+
+const char *launch_name(const sv_plan_s *p, const PlanLaunch &l) {
+    if (l.kind == 0) return gate1_kernel_name(p->h, p->pergate[size_t(l.index)]);
+    return tile_kernel_name(p->h);
+}
+
+}  // namespace
+
 }  // namespace sv
 
 using namespace sv;
@@ -49,13 +96,26 @@ sv_status sv_plan_create(sv_handle h, const char *text, int mode, sv_plan *out) 
     p->h = h;
     p->mode = mode;
     p->gates = int64_t(c.instrs.size());
-    if (mode == SV_MODE_PERGATE) {
-        p->pergate = lower_to_gate1(c);
-        for (const Gate1 &g : p->pergate) p->bytes += gate1_bytes(h, g);
-    } else {
+    const int tile_m = h->dt == SV_C64 ? kTileM64 : kTileM128;
+    if (mode == SV_MODE_FUSED) {
         delete p;
         set_error("mode %d is not available yet", mode);
         return SV_ERR_UNSUPPORTED;
+    }
+    if (mode == SV_MODE_PERGATE || h->n < tile_m) {
+        // per-gate updates (also the tiled mode's path for states smaller than one tile)
+        p->pergate = lower_to_gate1(c);
+        for (size_t i = 0; i < p->pergate.size(); ++i) {
+            const double b = gate1_bytes(h, p->pergate[i]);
+            p->launches.push_back(PlanLaunch{0, int(i), b});
+            p->bytes += b;
+        }
+    } else {
+        s = build_tile_plan(h, c, p);
+        if (s) {
+            destroy_plan(p);
+            return s;
+        }
     }
     h->live_plans++;
     *out = p;
@@ -67,8 +127,8 @@ sv_status sv_plan_execute(sv_plan p) {
         set_error("NULL plan");
         return SV_ERR_ARG;
     }
-    for (const Gate1 &g : p->pergate) {
-        sv_status s = check_launch(launch_gate1(p->h, g), "sv_plan_execute");
+    for (const PlanLaunch &l : p->launches) {
+        sv_status s = check_launch(launch_one(p, l), "sv_plan_execute");
         if (s) return s;
     }
     return SV_OK;
@@ -80,7 +140,7 @@ sv_status sv_plan_info(sv_plan p, int64_t *gates, int64_t *passes, double *bytes
         return SV_ERR_ARG;
     }
     if (gates) *gates = p->gates;
-    if (passes) *passes = int64_t(p->pergate.size());
+    if (passes) *passes = int64_t(p->launches.size());
     if (bytes) *bytes = p->bytes;
     return SV_OK;
 }
@@ -90,7 +150,7 @@ sv_status sv_plan_execute_timed(sv_plan p, void *const *events, int64_t n_events
         set_error("NULL argument");
         return SV_ERR_ARG;
     }
-    const int64_t passes = int64_t(p->pergate.size());
+    const int64_t passes = int64_t(p->launches.size());
     if (n_events < passes + 1) {
         set_error("need %lld events, got %lld", (long long)(passes + 1), (long long)n_events);
         return SV_ERR_ARG;
@@ -98,7 +158,7 @@ sv_status sv_plan_execute_timed(sv_plan p, void *const *events, int64_t n_events
     for (int64_t i = 0; i < passes; ++i) {
         cudaError_t e = cudaEventRecord(static_cast<cudaEvent_t>(events[i]), p->h->stream);
         if (e != cudaSuccess) return cuda_status(e, "cudaEventRecord");
-        sv_status s = check_launch(launch_gate1(p->h, p->pergate[size_t(i)]), "sv_plan_execute_timed");
+        sv_status s = check_launch(launch_one(p, p->launches[size_t(i)]), "sv_plan_execute_timed");
         if (s) return s;
     }
     cudaError_t e = cudaEventRecord(static_cast<cudaEvent_t>(events[passes]), p->h->stream);
@@ -106,10 +166,20 @@ sv_status sv_plan_execute_timed(sv_plan p, void *const *events, int64_t n_events
     return SV_OK;
 }
 
+sv_status sv_plan_launch_info(sv_plan p, int64_t i, const char **kernel, double *bytes) {
+    if (!p || i < 0 || i >= int64_t(p->launches.size())) {
+        set_error("bad plan or launch index");
+        return SV_ERR_ARG;
+    }
+    if (kernel) *kernel = launch_name(p, p->launches[size_t(i)]);
+    if (bytes) *bytes = p->launches[size_t(i)].bytes;
+    return SV_OK;
+}
+
 sv_status sv_plan_free(sv_plan p) {
     if (!p) return SV_OK;
     if (p->h) p->h->live_plans--;
-    delete p;
+    destroy_plan(p);
     return SV_OK;
 }
 

@@ -4,6 +4,7 @@
 #include <vector>
 
 #include "sv_internal.h"
+#include "tile.h"
 
 namespace sv {
 
@@ -17,12 +18,26 @@ cudaError_t launch_fused(sv_state *h, int k, const int *qubits, const double *U)
 // read + write of every amplitude the update changes).
 double gate1_bytes(const sv_state *h, const Gate1 &g);
 
+// Name of the kernel launch_gate1 picks for g.
+const char *gate1_kernel_name(const sv_state *h, const Gate1 &g);
+
 }  // namespace sv
+
+// One kernel launch of a plan.
+struct PlanLaunch {
+    int kind;      // 0: per-gate update pergate[index]; 1: tile pass tpasses[index]
+    int index;
+    double bytes;  // algorithmic bytes
+};
 
 struct sv_plan_s {
     sv_state *h = nullptr;
     int mode = 0;
-    int64_t gates = 0;                 // gates of the circuit text
-    std::vector<sv::Gate1> pergate;    // SV_MODE_PERGATE
-    double bytes = 0.0;                // algorithmic bytes of one execution
+    int64_t gates = 0;                     // gates of the circuit text
+    std::vector<sv::Gate1> pergate;        // per-gate updates
+    std::vector<sv::TilePassArgs> tpasses; // tile passes
+    void *d_ops = nullptr;                 // device copy of the tile ops
+    sv::TileSeg *d_segs = nullptr;         // device copy of the segment table
+    std::vector<PlanLaunch> launches;      // execution order
+    double bytes = 0.0;                    // algorithmic bytes of one execution
 };

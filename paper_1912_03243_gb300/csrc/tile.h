@@ -1,0 +1,125 @@
+// Tiled multi-gate passes: data structures shared by the host planner
+// (tile_plan.cpp) and the kernel (k_tile.cu).
+//
+// A pass picks m "tile" qubits.  Each CTA owns one tile: the 2^m amplitudes
+// whose other (outer) index bits equal the CTA's number, i.e. 2^(m-L) runs
+// of 2^L contiguous amplitudes (the tile always contains the low L qubits so
+// every HBM transfer is a contiguous run).  The CTA loads the tile into
+// shared memory once, applies every gate of the pass whose non-diagonal
+// qubits lie in the tile, and writes it back once: one HBM read and write of
+// the state per pass instead of one per gate.  Diagonal gates (T, CZ, CP)
+// need no qubit in the tile: an outer bit is a constant per CTA.
+//
+// Inside a pass, each thread holds 2^RB amplitudes in registers ("register
+// qubits"); a segment is a run of ops whose target qubits are register
+// qubits, and segments are separated by a shared-memory transposition that
+// changes which tile bits are register bits.
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+#include "sv_internal.h"
+
+namespace sv {
+
+constexpr int kTileMaxQ = 16;   // max tile bits
+constexpr int kTileMaxOuter = 40;
+
+enum TileOpType : int32_t {
+    TOP_G1 = 1,      // general 2x2 on register slot `a`
+    TOP_STRUCT = 2,  // structured 2x2 (entries 0, +-1, +-i): slot = a & 255, kind = a >> 8
+    TOP_PHASE = 3,   // multiply by u[0] + i u[1] where the condition holds; a = register condition id
+    TOP_NEG = 4,     // negate where the condition holds; a = register condition id
+    TOP_SEG = 5,     // start segment a (shared-memory transposition)
+    TOP_SCALE = 6,   // multiply every amplitude by u[0] + i u[1]
+};
+
+// Structured kinds: U = c * M with M below; c is deferred to a TOP_SCALE.
+enum StructKind : int32_t {
+    SK_H = 0,    // [[1, 1], [1, -1]]
+    SK_SX = 1,   // [[1, -i], [-i, 1]]
+    SK_SXD = 2,  // [[1, i], [i, 1]]
+    SK_SY = 3,   // [[1, -1], [1, 1]]
+    SK_SYD = 4,  // [[1, 1], [-1, 1]]
+    SK_X = 5,    // [[0, 1], [1, 0]]
+    SK_COUNT = 6
+};
+
+template <typename R>
+struct alignas(16) TileOp {
+    int32_t type;
+    int32_t a;
+    uint32_t rmask, rval;  // condition on the register index (TOP_G1 controls)
+    uint32_t tmask, tval;  // condition on the thread's tile-index bits
+    uint64_t gmask, gval;  // condition on the CTA's outer global index bits
+    R u[8];
+};
+
+struct TileSeg {
+    uint8_t rpos[8];            // tile-bit position of register slot s
+    uint8_t tpos[kTileMaxQ];    // tile-bit position of thread-index bit i (lane bits first)
+};
+
+struct TilePassArgs {
+    int n;
+    int m;                      // tile bits
+    int lc;                     // contiguous low tile bits (run length 2^lc)
+    int nouter;
+    uint8_t tile_pos[kTileMaxQ];     // global position of tile bit i (ascending)
+    uint8_t outer_pos[kTileMaxOuter];
+    int op_begin, op_end;
+};
+
+// Register-condition id used by TOP_PHASE / TOP_NEG: mask * 32 + value with
+// at most two mask bits.
+constexpr int reg_cond_id(uint32_t mask, uint32_t val) { return int(mask * 32 + val); }
+
+struct TileConfig {
+    int m;      // tile bits
+    int rb;     // register bits per thread
+    int low;    // low qubits always in the tile (contiguous runs of 2^low amplitudes)
+    bool c64;
+};
+
+template <typename R>
+struct TilePlan {
+    std::vector<TilePassArgs> passes;
+    std::vector<TileOp<R>> ops;
+    std::vector<TileSeg> segs;
+};
+
+// A gate in the planner's form.  kind 0: 2x2 update u on `target` where
+// the qubits in cmask equal cval (controls; full role on the target);
+// kind 1: multiply by u[0] where the qubits in cmask equal cval (diagonal).
+// `scale` is a global scalar factor deferred by the lowering (kind 1 with
+// cmask = 0 carries only that).
+struct PGate {
+    int kind;
+    int target;
+    uint64_t cmask, cval;
+    Cplx u[4];
+    Cplx scale;
+};
+
+// Circuit text -> planner gates (CZ/CP/T/P become diagonal phases, CX a
+// controlled X, SWAP three CX).
+std::vector<PGate> lower_for_tiles(const Circuit &circ);
+
+template <typename R>
+sv_status plan_tiles(const std::vector<PGate> &gates, int n, const TileConfig &cfg, TilePlan<R> *out);
+template <typename R>
+sv_status plan_tiles(const Circuit &circ, int n, const TileConfig &cfg, TilePlan<R> *out) {
+    return plan_tiles<R>(lower_for_tiles(circ), n, cfg, out);
+}
+
+// Tile geometry of the kernels: complex64 2^13-amplitude tiles with 32
+// amplitudes per thread, complex128 2^12 with 16.
+constexpr int kTileM64 = 13, kTileRB64 = 5, kTileLow64 = 4;
+constexpr int kTileM128 = 12, kTileRB128 = 4, kTileLow128 = 3;
+
+// Launch one pass over the whole state (grid = 2^(n-m) CTAs).
+cudaError_t launch_tile_pass(sv_state *h, const TilePassArgs &pa, const void *d_ops, const TileSeg *d_segs);
+const char *tile_kernel_name(const sv_state *h);
+
+}  // namespace sv

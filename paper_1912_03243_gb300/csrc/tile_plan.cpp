@@ -1,0 +1,374 @@
+// Host planner for tiled passes: lowers a circuit to tile ops, groups them
+// into HBM passes (greedy, dependency-respecting) and each pass into
+// register segments.  All modes compute the same ordered product of gates
+// (Sec. 2); the planner only reorders gates that commute (gates on disjoint
+// qubits, or diagonal gates), so the result is the circuit's.
+#include <algorithm>
+#include <cmath>
+#include <complex>
+
+#include "plan.h"
+#include "tile.h"
+
+namespace sv {
+
+namespace {
+
+using cd = std::complex<double>;
+
+cd toc(const Cplx &c) { return cd(c.re, c.im); }
+
+int popc(uint64_t x) { return __builtin_popcountll(x); }
+
+// Does U equal c * M_kind for a structured matrix M?  Returns the kind or -1.
+int struct_kind(const Cplx *u4, cd *scale) {
+    static const cd I(0, 1);
+    static const cd M[SK_COUNT][4] = {
+        {1, 1, 1, -1},         // H
+        {1, -I, -I, 1},        // SX
+        {1, I, I, 1},          // SXD
+        {1, -1, 1, 1},         // SY
+        {1, 1, -1, 1},         // SYD
+        {0, 1, 1, 0},          // X
+    };
+    cd u[4];
+    for (int k = 0; k < 4; ++k) u[k] = toc(u4[k]);
+    for (int kind = 0; kind < SK_COUNT; ++kind) {
+        int piv = -1;
+        for (int k = 0; k < 4; ++k)
+            if (M[kind][k] != cd(0)) {
+                piv = k;
+                break;
+            }
+        const cd c = u[piv] / M[kind][piv];
+        if (std::abs(c) == 0) continue;
+        bool ok = true;
+        for (int k = 0; k < 4 && ok; ++k) ok = std::abs(u[k] - c * M[kind][k]) <= 1e-15 * std::abs(c);
+        if (ok) {
+            *scale = c;
+            return kind;
+        }
+    }
+    return -1;
+}
+
+uint64_t full_of(const PGate &g) { return g.kind == 0 ? (uint64_t(1) << g.target) : 0; }
+uint64_t diag_of(const PGate &g) { return g.cmask; }
+
+bool conflicts(uint64_t F, uint64_t D, uint64_t bF, uint64_t bD) { return (F & (bF | bD)) || (D & bF); }
+
+}  // namespace
+
+std::vector<PGate> lower_for_tiles(const Circuit &c) {
+    std::vector<PGate> out;
+    Cplx m[16];
+    auto g1 = [&](int t, int ctl, const Cplx *u) {
+        PGate g{};
+        g.kind = 0;
+        g.target = t;
+        g.cmask = ctl >= 0 ? (uint64_t(1) << ctl) : 0;
+        g.cval = g.cmask;
+        for (int k = 0; k < 4; ++k) g.u[k] = u[k];
+        g.scale = Cplx{1, 0};
+        out.push_back(g);
+    };
+    auto phase = [&](uint64_t mask, uint64_t val, cd ph) {
+        if (ph == cd(1)) return;
+        PGate g{};
+        g.kind = 1;
+        g.target = -1;
+        g.cmask = mask;
+        g.cval = val;
+        g.u[0] = Cplx{ph.real(), ph.imag()};
+        g.scale = Cplx{1, 0};
+        out.push_back(g);
+    };
+    for (const Instr &ins : c.instrs) {
+        if (ins.nq == 1) {
+            gate_matrix(ins.name, ins.p, ins.np, m);
+            const bool diag = m[1].re == 0 && m[1].im == 0 && m[2].re == 0 && m[2].im == 0;
+            const uint64_t b = uint64_t(1) << ins.q[0];
+            if (diag) {
+                const cd d0 = toc(m[0]), d1 = toc(m[3]);
+                if (d0 == cd(0)) {
+                    phase(b, 0, 0);
+                    phase(b, b, d1);
+                } else {
+                    // diag(d0, d1) = d0 * diag(1, d1/d0): the scalar is deferred
+                    phase(b, b, d1 / d0);
+                    if (d0 != cd(1)) {
+                        PGate g{};
+                        g.kind = 1;
+                        g.target = -1;
+                        g.cmask = 0;
+                        g.cval = 0;
+                        g.u[0] = Cplx{1, 0};
+                        g.scale = Cplx{d0.real(), d0.imag()};
+                        out.push_back(g);
+                    }
+                }
+            } else {
+                g1(ins.q[0], -1, m);
+            }
+            continue;
+        }
+        const int a = ins.q[0], b = ins.q[1];
+        const uint64_t ab = (uint64_t(1) << a) | (uint64_t(1) << b);
+        if (ins.name == "CZ") {
+            phase(ab, ab, -1);
+        } else if (ins.name == "CP") {
+            phase(ab, ab, std::polar(1.0, ins.p[0]));
+        } else {
+            gate_matrix("X", nullptr, 0, m);
+            if (ins.name == "CX") {
+                g1(b, a, m);
+            } else {  // SWAP
+                g1(b, a, m);
+                g1(a, b, m);
+                g1(b, a, m);
+            }
+        }
+    }
+    return out;
+}
+
+namespace {
+
+// Lane order for the thread bits of a segment: the first lane bits get tile
+// positions whose shared-memory bank contributions are independent under the
+// XOR swizzle of k_tile (see phys_chunk there), the rest ascending.
+void order_thread_bits(const std::vector<int> &avail, bool c64, uint8_t *tpos) {
+    std::vector<int> rest = avail, lanes;
+    auto take = [&](auto pred) {
+        for (size_t i = 0; i < rest.size(); ++i)
+            if (pred(rest[i])) {
+                lanes.push_back(rest[i]);
+                rest.erase(rest.begin() + long(i));
+                return true;
+            }
+        return false;
+    };
+    if (c64) {
+        take([](int p) { return p == 0; });
+        for (int r = 0; r < 3; ++r) take([r](int p) { return p >= 1 && (p - 1) % 3 == r; });
+    } else {
+        for (int r = 0; r < 3; ++r) take([r](int p) { return p % 3 == r; });
+    }
+    std::sort(rest.begin(), rest.end());
+    size_t k = 0;
+    for (int p : lanes) tpos[k++] = uint8_t(p);
+    for (int p : rest) tpos[k++] = uint8_t(p);
+}
+
+}  // namespace
+
+template <typename R>
+sv_status plan_tiles(const std::vector<PGate> &G, int n, const TileConfig &cfg, TilePlan<R> *out) {
+    out->passes.clear();
+    out->ops.clear();
+    out->segs.clear();
+    const int m = cfg.m, rb = cfg.rb, L = cfg.low;
+    if (n < m) {
+        set_error("tiled mode needs n >= %d", m);
+        return SV_ERR_UNSUPPORTED;
+    }
+    std::vector<int> pending(G.size());
+    for (size_t i = 0; i < G.size(); ++i) pending[i] = int(i);
+    const uint64_t all = n == 64 ? ~uint64_t(0) : ((uint64_t(1) << n) - 1);
+    const uint64_t lowmask = (uint64_t(1) << L) - 1;
+
+    while (!pending.empty()) {
+        // ---- choose the tile qubits
+        uint64_t T = lowmask, bF = 0, bD = 0;
+        for (int idx : pending) {
+            const PGate &g = G[size_t(idx)];
+            const uint64_t F = full_of(g), D = diag_of(g);
+            if (conflicts(F, D, bF, bD)) {
+                bF |= F;
+                bD |= D;
+            } else {
+                const uint64_t need = F & ~T;
+                if (popc(T | need) <= m) T |= need;
+                else {
+                    bF |= F;
+                    bD |= D;
+                }
+            }
+            if ((bF & all) == all) break;
+        }
+        for (int q = 0; q < n && popc(T) < m; ++q) T |= uint64_t(1) << q;
+        // ---- collect the pass's gates
+        std::vector<int> pass_ops, rest;
+        bF = bD = 0;
+        for (size_t i = 0; i < pending.size(); ++i) {
+            const int idx = pending[i];
+            const PGate &g = G[size_t(idx)];
+            const uint64_t F = full_of(g), D = diag_of(g);
+            if ((bF & all) == all) {
+                rest.insert(rest.end(), pending.begin() + long(i), pending.end());
+                break;
+            }
+            if (!conflicts(F, D, bF, bD) && (F & ~T) == 0) pass_ops.push_back(idx);
+            else {
+                bF |= F;
+                bD |= D;
+                rest.push_back(idx);
+            }
+        }
+        pending.swap(rest);
+
+        TilePassArgs pa{};
+        pa.n = n;
+        pa.m = m;
+        int tpos_of[64];
+        for (int q = 0; q < 64; ++q) tpos_of[q] = -1;
+        {
+            int k = 0, o = 0;
+            for (int q = 0; q < n; ++q) {
+                if (T >> q & 1) {
+                    tpos_of[q] = k;
+                    pa.tile_pos[k++] = uint8_t(q);
+                } else {
+                    pa.outer_pos[o++] = uint8_t(q);
+                }
+            }
+            pa.nouter = o;
+            int lc = 0;
+            while (lc < m && pa.tile_pos[lc] == lc) ++lc;
+            pa.lc = lc;
+        }
+        pa.op_begin = int(out->ops.size());
+
+        // ---- segments (list scheduling over register slots)
+        std::vector<int> remaining = pass_ops;
+        cd scale = 1;
+        int since_flush = 0;
+        auto flush_scale = [&]() {
+            if (std::abs(scale - cd(1)) > 0) {
+                TileOp<R> op{};
+                op.type = TOP_SCALE;
+                op.u[0] = R(scale.real());
+                op.u[1] = R(scale.imag());
+                out->ops.push_back(op);
+            }
+            scale = 1;
+            since_flush = 0;
+        };
+        while (!remaining.empty()) {
+            uint64_t Rset = 0;
+            bF = bD = 0;
+            for (int idx : remaining) {
+                const PGate &g = G[size_t(idx)];
+                const uint64_t F = full_of(g), D = diag_of(g);
+                if (conflicts(F, D, bF, bD)) {
+                    bF |= F;
+                    bD |= D;
+                    continue;
+                }
+                const uint64_t need = F & ~Rset;
+                if (popc(Rset | need) <= rb) Rset |= need;
+                else {
+                    bF |= F;
+                    bD |= D;
+                }
+            }
+            for (int k = 0; k < m && popc(Rset) < rb; ++k) {
+                // fill with tile bits above 0 first (keeps tile bit 0 free for lanes)
+                const int p = (k + 1) % m;
+                Rset |= uint64_t(1) << pa.tile_pos[p];
+            }
+            std::vector<int> seg_ops, rest2;
+            bF = bD = 0;
+            for (int idx : remaining) {
+                const PGate &g = G[size_t(idx)];
+                const uint64_t F = full_of(g), D = diag_of(g);
+                if (!conflicts(F, D, bF, bD) && (F & ~Rset) == 0) seg_ops.push_back(idx);
+                else {
+                    bF |= F;
+                    bD |= D;
+                    rest2.push_back(idx);
+                }
+            }
+            remaining.swap(rest2);
+            // segment descriptor
+            TileSeg sg{};
+            int slot_of_tbit[kTileMaxQ];
+            for (int k = 0; k < kTileMaxQ; ++k) slot_of_tbit[k] = -1;
+            std::vector<int> rpos, avail;
+            for (int k = 0; k < m; ++k) {
+                if (Rset >> pa.tile_pos[k] & 1) rpos.push_back(k);
+                else avail.push_back(k);
+            }
+            for (size_t s = 0; s < rpos.size(); ++s) {
+                sg.rpos[s] = uint8_t(rpos[s]);
+                slot_of_tbit[rpos[s]] = int(s);
+            }
+            order_thread_bits(avail, cfg.c64, sg.tpos);
+            TileOp<R> segop{};
+            segop.type = TOP_SEG;
+            segop.a = int(out->segs.size());
+            out->segs.push_back(sg);
+            out->ops.push_back(segop);
+            // ops of the segment
+            for (int idx : seg_ops) {
+                const PGate &g = G[size_t(idx)];
+                TileOp<R> op{};
+                for (int q = 0; q < n; ++q) {
+                    if (!(g.cmask >> q & 1)) continue;
+                    const uint64_t want = g.cval >> q & 1;
+                    if (tpos_of[q] < 0) {
+                        op.gmask |= uint64_t(1) << q;
+                        op.gval |= want << q;
+                    } else if (slot_of_tbit[tpos_of[q]] >= 0) {
+                        op.rmask |= 1u << slot_of_tbit[tpos_of[q]];
+                        op.rval |= uint32_t(want) << slot_of_tbit[tpos_of[q]];
+                    } else {
+                        op.tmask |= 1u << tpos_of[q];
+                        op.tval |= uint32_t(want) << tpos_of[q];
+                    }
+                }
+                if (g.kind == 1) {
+                    if (toc(g.scale) != cd(1)) {  // a deferred scalar only
+                        scale *= toc(g.scale);
+                        continue;
+                    }
+                    const cd ph = toc(g.u[0]);
+                    op.type = ph == cd(-1) ? TOP_NEG : TOP_PHASE;
+                    op.a = reg_cond_id(op.rmask, op.rval);
+                    op.u[0] = R(ph.real());
+                    op.u[1] = R(ph.imag());
+                    out->ops.push_back(op);
+                    continue;
+                }
+                const int slot = slot_of_tbit[tpos_of[g.target]];
+                cd c;
+                const int kind = struct_kind(g.u, &c);
+                const bool controlled = g.cmask != 0;
+                if (kind >= 0 && (!controlled || c == cd(1))) {
+                    op.type = TOP_STRUCT;
+                    op.a = slot | (kind << 8);
+                    if (!controlled) scale *= c;
+                    out->ops.push_back(op);
+                    if (++since_flush >= 48) flush_scale();
+                } else {
+                    op.type = TOP_G1;
+                    op.a = slot;
+                    for (int k = 0; k < 4; ++k) {
+                        op.u[2 * k] = R(g.u[k].re);
+                        op.u[2 * k + 1] = R(g.u[k].im);
+                    }
+                    out->ops.push_back(op);
+                }
+            }
+        }
+        flush_scale();
+        pa.op_end = int(out->ops.size());
+        out->passes.push_back(pa);
+    }
+    return SV_OK;
+}
+
+template sv_status plan_tiles<float>(const std::vector<PGate> &, int, const TileConfig &, TilePlan<float> *);
+template sv_status plan_tiles<double>(const std::vector<PGate> &, int, const TileConfig &, TilePlan<double> *);
+
+}  // namespace sv

@@ -51,6 +51,7 @@ SIGNATURES = {
     "sv_plan_info": (_st, [_vp, _i64p, _i64p, _dp]),
     "sv_plan_execute_timed": (_st, [_vp, ctypes.POINTER(_vp), ctypes.c_int64]),
     "sv_plan_free": (_st, [_vp]),
+    "sv_plan_launch_info": (_st, [_vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_char_p), _dp]),
     "sv_encode2b": (_st, [_vp, _vp]),
     "sv_decode2b": (_st, [_vp, _vp]),
     "sv_get_codes": (_st, [_vp, ctypes.POINTER(ctypes.c_int8), ctypes.POINTER(ctypes.c_float)]),
@@ -152,6 +153,16 @@ class Plan:
         """events: list of torch.cuda.Event (passes + 1), recorded around each launch."""
         arr = (_vp * len(events))(*[_vp(e.cuda_event) for e in events])
         _check(lib().sv_plan_execute_timed(self.handle, arr, len(events)), "sv_plan_execute_timed")
+
+    def launch_info(self):
+        """[(kernel name, algorithmic bytes)] for every launch of one execution."""
+        out = []
+        name, b = ctypes.c_char_p(), ctypes.c_double()
+        for i in range(self.passes):
+            _check(lib().sv_plan_launch_info(self.handle, i, ctypes.byref(name), ctypes.byref(b)),
+                   "sv_plan_launch_info")
+            out.append((name.value.decode(), b.value))
+        return out
 
     def free(self) -> None:
         if self.handle:

@@ -1,0 +1,146 @@
+"""GPU parity of the tiled multi-gate passes against the CPU oracle (same
+tolerances as the per-gate path), from one tile (13 qubits) upwards, with
+every gate kind of the circuit format, and at the benchmark sizes through
+closed forms and the inverse-circuit round trip."""
+
+import math
+
+import numpy as np
+import pytest
+
+from paper_1912_03243_gb300 import circuits as C
+
+pytestmark = pytest.mark.gpu
+
+TOL_C128 = 1e-12
+TOL_C64_F = 1e-5
+TOL_C64_AMP = 1e-6
+
+
+@pytest.fixture(scope="module")
+def S():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1912_03243_gb300 import build, sv
+
+    build.build()
+    sv.lib()
+    return sv
+
+
+def fidelity(a, b):
+    return abs(np.vdot(a, b)) ** 2 / (np.vdot(a, a).real * np.vdot(b, b).real)
+
+
+def check(dtype, got, ref):
+    got = np.asarray(got, dtype=np.complex128)
+    if dtype == "c128":
+        assert np.max(np.abs(got - ref)) <= TOL_C128
+    else:
+        nrm = math.sqrt(np.vdot(ref, ref).real)
+        assert np.max(np.abs(got - ref)) <= TOL_C64_AMP * nrm
+        assert 1 - fidelity(ref, got) <= TOL_C64_F
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+@pytest.mark.parametrize("n,depth,seed", [(13, 12, 1), (14, 20, 2), (16, 20, 3), (20, 20, 1)])
+def test_random_circuit(S, orc, dtype, n, depth, seed):
+    c = C.random_circuit(n, depth, seed)
+    ref = orc.run(c)
+    s = S.StateVector(n, dtype)
+    p = s.plan(c, "tiled")
+    assert p.passes < len(c)
+    p.execute()
+    check(dtype, s.to_numpy(), ref)
+    p.free()
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+@pytest.mark.parametrize("n,seed", [(13, 5), (15, 6), (18, 7)])
+def test_every_gate_kind(S, orc, dtype, n, seed):
+    """U, P, S, T, X, Y, Z, SX/SY and adjoints, CZ, CX, CP, SWAP on random
+    qubits: exercises general, structured, controlled and diagonal ops with
+    conditions on register, thread and CTA index bits."""
+    c = C.random_unitary_gates(n, 400, seed)
+    ref = orc.run(c)
+    s = S.StateVector(n, dtype)
+    s.run(c, "tiled")
+    check(dtype, s.to_numpy(), ref)
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_ghz_qft_uniform(S, orc, dtype):
+    n = 18
+    for c in (C.ghz_circuit(n), C.qft_circuit(n, 0x2B6D1), C.uniform_circuit(n)):
+        s = S.StateVector(n, dtype)
+        s.run(c, "tiled")
+        check(dtype, s.to_numpy(), orc.run(c))
+
+
+def test_small_state_uses_per_gate_path(S, orc):
+    c = C.random_circuit(8, 6, 2)
+    s = S.StateVector(8, "c64")
+    p = s.plan(c, "tiled")
+    assert p.passes == p.gates  # below one tile every launch is a per-gate update
+    p.execute()
+    check("c64", s.to_numpy(), orc.run(c))
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_24q_against_oracle(S, orc, dtype):
+    c = C.random_circuit(24, 16, 1)
+    s = S.StateVector(24, dtype)
+    s.run(c, "tiled")
+    check(dtype, s.to_numpy(), orc.run(c))
+
+
+def test_tiled_equals_pergate_c64(S):
+    c = C.random_circuit(22, 16, 9)
+    a = S.StateVector(22, "c64")
+    a.run(c, "tiled")
+    b = S.StateVector(22, "c64")
+    b.run(c, "pergate")
+    x, y = a.to_numpy().astype(np.complex128), b.to_numpy().astype(np.complex128)
+    assert np.max(np.abs(x - y)) < 1e-6
+    assert 1 - fidelity(x, y) < 1e-6
+
+
+def test_benchmark_size_32q(S):
+    """The 32-qubit benchmark workload: the depth-24 random circuit followed
+    by its inverse returns to |0...0> (1 - F <= 1e-5), and the 32-qubit QFT of
+    a basis state matches its closed form at sampled outputs."""
+    import torch
+
+    n = 32
+    if torch.cuda.mem_get_info()[0] < (8 << n) + (4 << 30):
+        pytest.skip("not enough device memory")
+    s = S.StateVector(n, "c64")
+    c = C.random_circuit(n, 24, 1)
+    s.run(c, "tiled")
+    assert abs(s.norm() - 1) < 1e-4
+    s.run(C.inverse_circuit(c), "tiled")
+    a = s.amplitudes([0, 1, 12345, (1 << n) - 1])
+    assert 1 - abs(a[0]) ** 2 <= TOL_C64_F
+    assert np.max(np.abs(a[1:])) <= TOL_C64_AMP
+    x = 0x9E3779B9
+    s.set_basis(x)
+    s.run(C.qft_circuit(n), "tiled")
+    y = np.random.default_rng(2).integers(0, 1 << n, size=4096, dtype=np.uint64)
+    got = s.amplitudes(y)
+    ph = ((x * y.astype(object)) % (1 << n)).astype(np.float64) / (1 << n)
+    expect = np.exp(2j * np.pi * ph) / math.sqrt(1 << n)
+    assert np.max(np.abs(got - expect)) <= TOL_C64_AMP
+    del s
+    torch.cuda.empty_cache()
+
+
+def test_30q_c128_roundtrip(S):
+    n = 30
+    s = S.StateVector(n, "c128")
+    c = C.random_circuit(n, 16, 1)
+    s.run(c, "tiled")
+    s.run(C.inverse_circuit(c), "tiled")
+    a = s.amplitudes([0, 5, (1 << n) - 1])
+    assert abs(a[0] - 1) < 1e-11 and np.max(np.abs(a[1:])) < 1e-11
