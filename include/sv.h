@@ -182,6 +182,24 @@ sv_status sv_norm(sv_handle h, double *out);
 sv_status sv_copy_to_host(sv_handle h, void *dst, size_t bytes);
 sv_status sv_copy_from_host(sv_handle h, const void *src, size_t bytes);
 
+/* Gather m amplitudes from caller-owned device memory without allocating any
+ * device memory (the paper has no counterpart; this is a library service).
+ * For callers that cannot call cudaMalloc -- an allocator that owns all of
+ * HBM, a state that fills the device, a loop that must not hit cudaMalloc's
+ * implicit synchronisation -- and so cannot create a handle either (handles
+ * hold cudaMalloc'ed scratch).  state: device pointer to an n-qubit state in
+ * the dtype layout above; idx: m host indices < 2^n; out: 2m host doubles
+ * (re, im).  At most 65536 indices per call (larger m is rejected with
+ * SV_ERR_ARG and a message); the index list and results pass through one
+ * fixed 1.5 MiB file-scope device array that every GPU loading the library
+ * holds until exit.  The first call on a device looks up that array's device
+ * address (cudaGetSymbolAddress) with the device current, so make the first
+ * call before any stream capture.  Every call shares the array: calls that
+ * overlap on the GPU (other threads, other streams) race.  Synchronises the
+ * stream.  Errors: SV_ERR_ARG, SV_ERR_CUDA. */
+sv_status sv_amplitudes_noalloc(const void *state, int n, sv_dtype dt, size_t m, const uint64_t *idx,
+                                double *out, void *stream);
+
 /* ---- decomposition of entangling gates (Sec. 4) ---------------------------------- */
 
 /* Eq. 3: <z|C|0> for m bit strings z of an n-qubit circuit C (n <= 64),

@@ -57,6 +57,7 @@ SIGNATURES = {
     "sv_get_codes": (_st, [_vp, ctypes.POINTER(ctypes.c_int8), ctypes.POINTER(ctypes.c_float)]),
     "sv_amplitudes": (_st, [_vp, ctypes.c_size_t, _u64p, _dp]),
     "sv_norm": (_st, [_vp, _dp]),
+    "sv_amplitudes_noalloc": (_st, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_size_t, _u64p, _dp, _vp]),
     "sv_copy_to_host": (_st, [_vp, _vp, ctypes.c_size_t]),
     "sv_copy_from_host": (_st, [_vp, _vp, ctypes.c_size_t]),
     "sv_cut_amplitudes": (_st, [ctypes.c_char_p, ctypes.c_int, ctypes.c_uint64, ctypes.c_int, ctypes.c_size_t,
@@ -132,6 +133,21 @@ def sv_cut_amplitudes(circuit, n: int, mask_a: int, z, form: int = 0, stream=Non
                                    zz.ctypes.data_as(_u64p), _dptr(out), ctypes.byref(s), _vp(st)),
            "sv_cut_amplitudes")
     return out.view(np.complex128).copy(), s.value
+
+
+def sv_amplitudes_noalloc(state_ptr: int, n: int, dtype: str | int, idx, stream=None) -> np.ndarray:
+    """Gather amplitudes from a raw device pointer without any device
+    allocation (scratch lives in a fixed device array inside the library)."""
+    ii = np.ascontiguousarray(idx, dtype=np.uint64)
+    out = np.zeros(2 * ii.size, dtype=np.float64)
+    if stream is None:
+        import torch
+
+        stream = torch.cuda.current_stream().cuda_stream
+    _check(lib().sv_amplitudes_noalloc(_vp(state_ptr), n, DTYPES.get(dtype, dtype), ii.size,
+                                       ii.ctypes.data_as(_u64p), _dptr(out), _vp(stream)),
+           "sv_amplitudes_noalloc")
+    return out.view(np.complex128).copy()
 
 
 class Plan:
