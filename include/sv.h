@@ -155,6 +155,15 @@ sv_status sv_plan_free(sv_plan p);
  * the algorithmic bytes it moves.  *kernel points to a static string. */
 sv_status sv_plan_launch_info(sv_plan p, int64_t i, const char **kernel, double *bytes);
 
+/* Host only (no GPU needed): plan a circuit for SV_MODE_TILED and report its
+ * gate count, HBM passes and register segments; with compile != 0 also
+ * compile every pass for sm_103a (the tiled mode compiles one straight-line
+ * kernel per pass with NVRTC when a plan is created).  n >= 13 (SV_C64) or
+ * n >= 12 (SV_C128).  Errors: SV_ERR_PARSE, SV_ERR_ARG, SV_ERR_UNSUPPORTED,
+ * SV_ERR_CUDA (compile failure). */
+sv_status sv_plan_stats(const char *text, int n, sv_dtype dt, int compile, int64_t *gates, int64_t *passes,
+                        int64_t *segments);
+
 /* ---- two-byte encoding (Sec. 1 and Sec. 3) ---------------------------------- */
 
 /* Encode an SV_C64 state into an SV_ENC2B state of the same n (blocks of 256,

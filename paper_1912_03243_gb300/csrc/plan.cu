@@ -20,23 +20,15 @@ double gate1_bytes(const sv_state *h, const Gate1 &g) {
 
 namespace {
 
-void destroy_plan(sv_plan_s *p) {
-    if (p->d_ops) cudaFree(p->d_ops);
-    if (p->d_segs) cudaFree(p->d_segs);
-    delete p;
-}
+void destroy_plan(sv_plan_s *p) { delete p; }
 
 template <typename R>
 sv_status upload_tile_plan(sv_plan_s *p, const TilePlan<R> &tp) {
-    p->tpasses = tp.passes;
-    const size_t ob = tp.ops.size() * sizeof(TileOp<R>), sb = tp.segs.size() * sizeof(TileSeg);
-    SV_CUDA_TRY(cudaMalloc(&p->d_ops, ob > 0 ? ob : 16));
-    SV_CUDA_TRY(cudaMalloc(&p->d_segs, sb > 0 ? sb : 16));
-    if (ob) SV_CUDA_TRY(cudaMemcpy(p->d_ops, tp.ops.data(), ob, cudaMemcpyHostToDevice));
-    if (sb) SV_CUDA_TRY(cudaMemcpy(p->d_segs, tp.segs.data(), sb, cudaMemcpyHostToDevice));
+    sv_status s = jit_tile_plan(tp, &p->tfns);
+    if (s) return s;
     const double pass_bytes = 2.0 * double(uint64_t(1) << p->h->n) * (p->h->dt == SV_C64 ? 8.0 : 16.0);
     for (size_t i = 0; i < tp.passes.size(); ++i) {
-        p->launches.push_back(PlanLaunch{1, int(i), pass_bytes});
+        p->launches.push_back(PlanLaunch{1, int(i), pass_bytes});  // compiled pass i
         p->bytes += pass_bytes;
     }
     return SV_OK;
@@ -55,7 +47,7 @@ sv_status build_tile_plan(sv_state *h, const Circuit &c, sv_plan_s *p) {
 
 cudaError_t launch_one(sv_plan_s *p, const PlanLaunch &l) {
     if (l.kind == 0) return launch_gate1(p->h, p->pergate[size_t(l.index)]);
-    return launch_tile_pass(p->h, p->tpasses[size_t(l.index)], p->d_ops, p->d_segs);
+    return launch_jit_pass(p->h, p->tfns[size_t(l.index)], p->h->n);
 }
 
 const char *launch_name(const sv_plan_s *p, const PlanLaunch &l) {
@@ -174,6 +166,41 @@ sv_status sv_plan_launch_info(sv_plan p, int64_t i, const char **kernel, double 
     if (kernel) *kernel = launch_name(p, p->launches[size_t(i)]);
     if (bytes) *bytes = p->launches[size_t(i)].bytes;
     return SV_OK;
+}
+
+sv_status sv_plan_stats(const char *text, int n, sv_dtype dt, int compile, int64_t *gates, int64_t *passes,
+                        int64_t *segments) {
+    if (!text || n < 1 || n > kMaxQubits || (dt != SV_C64 && dt != SV_C128)) {
+        set_error("bad arguments");
+        return SV_ERR_ARG;
+    }
+    Circuit c;
+    sv_status s = parse_circuit(text, n, &c);
+    if (s) return s;
+    if (gates) *gates = int64_t(c.instrs.size());
+    auto count = [&](auto &tp) -> sv_status {
+        int64_t segs = 0;
+        for (const auto &op : tp.ops) segs += op.type == TOP_SEG;
+        if (passes) *passes = int64_t(tp.passes.size());
+        if (segments) *segments = segs;
+        return compile ? jit_compile_check(tp) : SV_OK;
+    };
+    if (dt == SV_C64) {
+        if (n < kTileM64) {
+            set_error("tiled passes need n >= %d", kTileM64);
+            return SV_ERR_UNSUPPORTED;
+        }
+        TilePlan<float> tp;
+        s = plan_tiles<float>(c, n, TileConfig{kTileM64, kTileRB64, kTileLow64, true}, &tp);
+        return s ? s : count(tp);
+    }
+    if (n < kTileM128) {
+        set_error("tiled passes need n >= %d", kTileM128);
+        return SV_ERR_UNSUPPORTED;
+    }
+    TilePlan<double> tp;
+    s = plan_tiles<double>(c, n, TileConfig{kTileM128, kTileRB128, kTileLow128, false}, &tp);
+    return s ? s : count(tp);
 }
 
 sv_status sv_plan_free(sv_plan p) {

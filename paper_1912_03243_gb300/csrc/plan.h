@@ -25,7 +25,7 @@ const char *gate1_kernel_name(const sv_state *h, const Gate1 &g);
 
 // One kernel launch of a plan.
 struct PlanLaunch {
-    int kind;      // 0: per-gate update pergate[index]; 1: tile pass tpasses[index]
+    int kind;      // 0: per-gate update pergate[index]; 1: compiled tile pass tfns[index]
     int index;
     double bytes;  // algorithmic bytes
 };
@@ -35,9 +35,7 @@ struct sv_plan_s {
     int mode = 0;
     int64_t gates = 0;                     // gates of the circuit text
     std::vector<sv::Gate1> pergate;        // per-gate updates
-    std::vector<sv::TilePassArgs> tpasses; // tile passes
-    void *d_ops = nullptr;                 // device copy of the tile ops
-    sv::TileSeg *d_segs = nullptr;         // device copy of the segment table
+    std::vector<void *> tfns;              // compiled tile passes (CUfunction)
     std::vector<PlanLaunch> launches;      // execution order
     double bytes = 0.0;                    // algorithmic bytes of one execution
 };

@@ -119,6 +119,7 @@ int sv_num_qubits(sv_handle h) { return h ? h->n : -1; }
 int sv_dtype_of(sv_handle h) { return h ? int(h->dt) : -1; }
 
 static sv_status finish_init(sv_state *h) {
+    SV_CUDA_TRY(cudaGetDevice(&h->device));
     if (h->dt == SV_ENC2B) h->scales = reinterpret_cast<float *>(static_cast<char *>(h->data) + (size_t(2) << h->n));
     return init_scratch(h);
 }

@@ -81,6 +81,7 @@ struct sv_state {
     size_t bytes = 0;
     bool owned = false;
     cudaStream_t stream = nullptr;
+    int device = 0;
     // scratch (library-owned, small)
     double *d_partials = nullptr;  // norm partial sums
     int partials_cap = 0;

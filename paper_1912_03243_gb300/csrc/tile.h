@@ -118,8 +118,15 @@ sv_status plan_tiles(const Circuit &circ, int n, const TileConfig &cfg, TilePlan
 constexpr int kTileM64 = 13, kTileRB64 = 5, kTileLow64 = 4;
 constexpr int kTileM128 = 12, kTileRB128 = 4, kTileLow128 = 3;
 
-// Launch one pass over the whole state (grid = 2^(n-m) CTAs).
-cudaError_t launch_tile_pass(sv_state *h, const TilePassArgs &pa, const void *d_ops, const TileSeg *d_segs);
+// Compile every pass of a plan into a straight-line kernel (NVRTC, cached
+// per device and source); fns receives one CUfunction per pass.
+sv_status jit_tile_plan(const TilePlan<float> &tp, std::vector<void *> *fns);
+sv_status jit_tile_plan(const TilePlan<double> &tp, std::vector<void *> *fns);
+// Compile only (no device needed): NVRTC-compiles every pass, returns status.
+sv_status jit_compile_check(const TilePlan<float> &tp);
+sv_status jit_compile_check(const TilePlan<double> &tp);
+// Launch one compiled pass over the whole state (grid = 2^(n-m) CTAs).
+cudaError_t launch_jit_pass(sv_state *h, void *fn, int n);
 const char *tile_kernel_name(const sv_state *h);
 
 }  // namespace sv

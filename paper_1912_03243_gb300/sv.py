@@ -51,6 +51,7 @@ SIGNATURES = {
     "sv_plan_info": (_st, [_vp, _i64p, _i64p, _dp]),
     "sv_plan_execute_timed": (_st, [_vp, ctypes.POINTER(_vp), ctypes.c_int64]),
     "sv_plan_free": (_st, [_vp]),
+    "sv_plan_stats": (_st, [ctypes.c_char_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, _i64p, _i64p, _i64p]),
     "sv_plan_launch_info": (_st, [_vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_char_p), _dp]),
     "sv_encode2b": (_st, [_vp, _vp]),
     "sv_decode2b": (_st, [_vp, _vp]),
@@ -133,6 +134,14 @@ def sv_cut_amplitudes(circuit, n: int, mask_a: int, z, form: int = 0, stream=Non
                                    zz.ctypes.data_as(_u64p), _dptr(out), ctypes.byref(s), _vp(st)),
            "sv_cut_amplitudes")
     return out.view(np.complex128).copy(), s.value
+
+
+def sv_plan_stats(circuit, n: int, dtype: str | int = "c64", compile: bool = False):
+    """Host-only tiled planning statistics: (gates, passes, segments)."""
+    g, p, s = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().sv_plan_stats(_text(circuit), n, DTYPES.get(dtype, dtype), int(compile), ctypes.byref(g),
+                               ctypes.byref(p), ctypes.byref(s)), "sv_plan_stats")
+    return g.value, p.value, s.value
 
 
 def sv_amplitudes_noalloc(state_ptr: int, n: int, dtype: str | int, idx, stream=None) -> np.ndarray:

@@ -86,3 +86,16 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(sv, "LIB_PATH", str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError, match="not built"):
         sv.lib()
+
+
+def test_tiled_plans_compile_for_sm103a(L):
+    """The tiled mode emits one straight-line kernel per pass; planning and
+    NVRTC compilation need no GPU.  Pass counts of the benchmark circuits."""
+    g, p, s = sv.sv_plan_stats(C.random_circuit(14, 6, 1), 14, "c64", compile=True)
+    assert g == 14 * 6 + 3 * 7 + 3 * 6 and 1 <= p < g and s >= p
+    g, p, s = sv.sv_plan_stats(C.random_unitary_gates(13, 120, 4), 13, "c128", compile=True)
+    assert p >= 1
+    g, p, s = sv.sv_plan_stats(C.random_circuit(32, 24, 1), 32, "c64")
+    assert g == 1140 and p <= 30
+    with pytest.raises(sv.SVError):
+        sv.sv_plan_stats(C.random_circuit(8, 2, 1), 8, "c64")
