@@ -23,6 +23,7 @@
 #include <nvrtc.h>
 
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <functional>
 #include <mutex>
@@ -86,6 +87,14 @@ struct Geo {
     }
 };
 
+// CTAs per SM the pass kernels are compiled for (register budget); the
+// shared tile (64 KiB) allows up to 3.  SV_TILE_CTAS overrides.
+int tile_ctas_per_sm() {
+    const char *e = std::getenv("SV_TILE_CTAS");
+    const int v = e ? std::atoi(e) : 2;
+    return v >= 1 && v <= 3 ? v : 2;
+}
+
 template <typename R>
 std::string gen_pass(const TilePlan<R> &tp, size_t pass) {
     using G = Geo<R>;
@@ -98,7 +107,7 @@ std::string gen_pass(const TilePlan<R> &tp, size_t pass) {
     o << "__device__ __forceinline__ void cpa16(void* s, const void* g) {\n"
          "  u32 sa = (u32)__cvta_generic_to_shared(s);\n"
          "  asm volatile(\"cp.async.cg.shared.global [%0], [%1], 16;\\n\" :: \"r\"(sa), \"l\"(g) : \"memory\");\n}\n";
-    o << "extern \"C\" __global__ void __launch_bounds__(" << G::NT << ", 2) svp(" << C2T
+    o << "extern \"C\" __global__ void __launch_bounds__(" << G::NT << ", " << tile_ctas_per_sm() << ") svp(" << C2T
       << "* __restrict__ psi) {\n";
     o << "  extern __shared__ __align__(16) unsigned char smem[];\n";
     o << "  " << C2T << "* sm = reinterpret_cast<" << C2T << "*>(smem);\n";

@@ -160,6 +160,70 @@ void order_thread_bits(const std::vector<int> &avail, bool c64, uint8_t *tpos) {
     for (int p : rest) tpos[k++] = uint8_t(p);
 }
 
+
+// Number of pending gates applicable in one pass with tile set T (a gate is
+// applicable when its non-diagonal qubit is in T and no earlier pending gate
+// it does not commute with stays behind).
+int count_applicable(const std::vector<PGate> &G, const std::vector<int> &pending, uint64_t T, uint64_t all) {
+    uint64_t bF = 0, bD = 0;
+    int cnt = 0;
+    for (int idx : pending) {
+        const PGate &g = G[size_t(idx)];
+        const uint64_t F = full_of(g), D = diag_of(g);
+        if (!conflicts(F, D, bF, bD) && (F & ~T) == 0) ++cnt;
+        else {
+            bF |= F;
+            bD |= D;
+            if ((bF & all) == all) break;
+        }
+    }
+    return cnt;
+}
+
+uint64_t choose_tile(const std::vector<PGate> &G, const std::vector<int> &pending, int n, int m, uint64_t lowmask,
+                     uint64_t all) {
+    // (a) first-come
+    uint64_t Ta = lowmask, bF = 0, bD = 0;
+    for (int idx : pending) {
+        const PGate &g = G[size_t(idx)];
+        const uint64_t F = full_of(g), D = diag_of(g);
+        if (conflicts(F, D, bF, bD)) {
+            bF |= F;
+            bD |= D;
+        } else {
+            const uint64_t need = F & ~Ta;
+            if (popc(Ta | need) <= m) Ta |= need;
+            else {
+                bF |= F;
+                bD |= D;
+            }
+        }
+        if ((bF & all) == all) break;
+    }
+    for (int q = 0; q < n && popc(Ta) < m; ++q) Ta |= uint64_t(1) << q;
+    // (b) greedy growth by applicable-gate count; ties go to the qubit whose
+    // first pending non-diagonal gate comes earliest
+    std::vector<int> first_use(size_t(n), 1 << 30);
+    for (size_t i = 0; i < pending.size(); ++i) {
+        const PGate &g = G[size_t(pending[i])];
+        if (g.kind == 0 && first_use[size_t(g.target)] > int(i)) first_use[size_t(g.target)] = int(i);
+    }
+    uint64_t Tb = lowmask;
+    while (popc(Tb) < m && popc(Tb) < n) {
+        int best_q = -1, best_c = -1;
+        for (int q = 0; q < n; ++q) {
+            if (Tb >> q & 1) continue;
+            const int c = count_applicable(G, pending, Tb | (uint64_t(1) << q), all);
+            if (c > best_c || (c == best_c && first_use[size_t(q)] < first_use[size_t(best_q)])) {
+                best_c = c;
+                best_q = q;
+            }
+        }
+        Tb |= uint64_t(1) << best_q;
+    }
+    return count_applicable(G, pending, Tb, all) >= count_applicable(G, pending, Ta, all) ? Tb : Ta;
+}
+
 }  // namespace
 
 template <typename R>
@@ -178,28 +242,13 @@ sv_status plan_tiles(const std::vector<PGate> &G, int n, const TileConfig &cfg, 
     const uint64_t lowmask = (uint64_t(1) << L) - 1;
 
     while (!pending.empty()) {
-        // ---- choose the tile qubits
-        uint64_t T = lowmask, bF = 0, bD = 0;
-        for (int idx : pending) {
-            const PGate &g = G[size_t(idx)];
-            const uint64_t F = full_of(g), D = diag_of(g);
-            if (conflicts(F, D, bF, bD)) {
-                bF |= F;
-                bD |= D;
-            } else {
-                const uint64_t need = F & ~T;
-                if (popc(T | need) <= m) T |= need;
-                else {
-                    bF |= F;
-                    bD |= D;
-                }
-            }
-            if ((bF & all) == all) break;
-        }
-        for (int q = 0; q < n && popc(T) < m; ++q) T |= uint64_t(1) << q;
+        // ---- choose the tile qubits: the better of (a) first-come (qubits in
+        // the order pending gates need them) and (b) greedy growth, adding
+        // one qubit at a time the one that makes the most gates applicable
+        const uint64_t T = choose_tile(G, pending, n, m, lowmask, all);
         // ---- collect the pass's gates
         std::vector<int> pass_ops, rest;
-        bF = bD = 0;
+        uint64_t bF = 0, bD = 0;
         for (size_t i = 0; i < pending.size(); ++i) {
             const int idx = pending[i];
             const PGate &g = G[size_t(idx)];
