@@ -1,0 +1,376 @@
+// Dense k-qubit block (Sec. 2: a gate on k qubits is a 2^k x 2^k matrix on
+// the amplitudes that differ only in those qubits) on the 5th-generation
+// tensor cores, complex64 state.
+//
+// Real expansion: with amplitudes interleaved (re, im), the complex block U
+// acts as the 2d x 2d real matrix Ut, Ut[2r+a][2c+b] = [[Re, -Im], [Im, Re]]
+// of U[r][c] (d = 2^k).  A = I_P (x) Ut (P = 64/d copies on the diagonal) is
+// always 128 x 128, so one MMA shape (M = N = 128, K = 16 per instruction)
+// serves every k <= 6; column n of B holds P groups of d amplitudes.
+//
+// Split precision: A = Ah + Al and B = Bh + Bl with BF16 parts (Ah = bf16(A),
+// Al = bf16(A - Ah)); D = Ah Bh + Ah Bl + Al Bh accumulates in FP32 in tensor
+// memory (relative error about 2^-16 per product instead of 2^-8).
+//
+// Per CTA (persistent, one per SM, 256 threads) and per tile of 2^13
+// amplitudes (the k block qubits plus the lowest other qubits):
+//   cp.async the tile into shared memory (FP32) -> convert to Bh, Bl in the
+//   K-major no-swizzle canonical layout -> one thread issues 3 x 8
+//   tcgen05.mma (K = 16 each) into a 128-column TMEM accumulator and commits
+//   to an mbarrier -> all threads wait (bounded by %globaltimer) -> each warp
+//   reads its 32 TMEM lanes with tcgen05.ld and scatters FP32 results back to
+//   the shared tile -> coalesced 16-byte stores to HBM.
+// Operand layout (both K-major, no swizzle): element (row, kk) at byte
+// (row%8)*16 + (kk%8)*2 + (kk/8)*128 + (row/8)*2048; leading-dimension byte
+// offset 128 (next 8 K-elements), stride-dimension byte offset 2048 (next 8
+// rows); the K-slice s of an instruction starts at + 256 s.
+#include <cuda_bf16.h>
+
+#include <cstring>
+#include <vector>
+
+#include "plan.h"
+
+namespace sv {
+namespace {
+
+constexpr int kTcM = 13;          // tile bits
+constexpr int kTcThreads = 256;
+constexpr int kTcCols = 128;      // TMEM columns of the accumulator (N)
+constexpr uint32_t kOpBytes = 128 * 128 * 2;  // one BF16 operand (32 KiB)
+
+struct TcArgs {
+    int n, k, P;
+    int nouter;
+    int lc;
+    uint64_t ntiles;
+    long long timeout_ns;
+    int skip_mma;                 // test hook: never issue the MMA (the wait must time out)
+    uint8_t tile_pos[kTcM];
+    uint8_t outer_pos[40];
+    uint16_t offL[64];            // tile index offset of block-local index l
+    uint16_t offP[64];            // tile index offset of pack p
+    uint16_t offN[128];           // tile index offset of column n
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return uint32_t(__cvta_generic_to_shared(p)); }
+
+__device__ __forceinline__ void cp_async16(uint32_t saddr, const void *g) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(saddr), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+__device__ __forceinline__ uint64_t globaltimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Shared-memory matrix descriptor: start >> 4 (bits 0-13), LBO >> 4 (16-29),
+// SBO >> 4 (32-45), fixed 0b001 at bits 46-48, base offset 0, no swizzle.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = uint64_t((saddr >> 4) & 0x3FFFu);
+    d |= uint64_t((lbo >> 4) & 0x3FFFu) << 16;
+    d |= uint64_t((sbo >> 4) & 0x3FFFu) << 32;
+    d |= uint64_t(1) << 46;
+    return d;
+}
+
+// Instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16
+// (bits 7-9 = 1, 10-12 = 1), both K-major, N >> 3 at bits 17-22, M >> 4 at
+// bits 24-28.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accum) {
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accum)
+        : "memory");
+}
+
+__device__ __forceinline__ uint16_t bf16_bits(__nv_bfloat16 h) { return *reinterpret_cast<uint16_t *>(&h); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1) k_fused_tc(float2 *__restrict__ psi, const uint4 *__restrict__ gA,
+                                                            int *__restrict__ err, const TcArgs a) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char *sAh = smem, *sAl = smem + kOpBytes;
+    unsigned char *sBh = smem + 2 * kOpBytes, *sBl = smem + 3 * kOpBytes;
+    float2 *sX = reinterpret_cast<float2 *>(smem + 4 * kOpBytes);  // 2^13 amplitudes (64 KiB)
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tmem_slot;
+    __shared__ int abort_flag;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t mbar_a = smem_u32(&mbar);
+
+    if (tid == 0) {
+        abort_flag = 0;
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mbar_a) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(kTcCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    // the A operands (Ah then Al, 64 KiB) are the same for every tile
+    for (int i = tid; i < int(2 * kOpBytes / 16); i += kTcThreads) cp_async16(smem_u32(smem + 16 * i), gA + i);
+    cp_async_wait_all();
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+
+    const uint32_t lmask = (1u << a.lc) - 1u;
+    uint32_t phase = 0;
+    for (uint64_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+        uint64_t base = 0;
+        for (int q = 0; q < a.nouter; ++q) base |= ((tile >> q) & 1ull) << a.outer_pos[q];
+        // load: 16-byte chunks (2 amplitudes), tile index j = 2c
+        for (int c = tid; c < (1 << (kTcM - 1)); c += kTcThreads) {
+            const uint32_t j = uint32_t(c) * 2;
+            uint64_t g = base | (j & lmask);
+            for (int q = a.lc; q < kTcM; ++q) g |= uint64_t((j >> q) & 1u) << a.tile_pos[q];
+            cp_async16(smem_u32(sX + j), psi + g);
+        }
+        cp_async_wait_all();
+        __syncthreads();
+        // convert: one task = one B row n and 8 consecutive K elements (16 B of Bh and of Bl)
+        const int twoD = 2 << a.k;
+        for (int t = tid; t < 16 * 128; t += kTcThreads) {
+            const int nrow = t & 127, q8 = t >> 7;
+            uint32_t hw[4], lw[4];
+#pragma unroll
+            for (int e = 0; e < 8; e += 2) {
+                uint16_t hb[2], lb[2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int kk = q8 * 8 + e + h;
+                    const int p = kk / twoD, r = kk % twoD;
+                    const float2 amp = sX[a.offL[r >> 1] | a.offP[p] | a.offN[nrow]];
+                    const float x = (r & 1) ? amp.y : amp.x;
+                    const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+                    const __nv_bfloat16 lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+                    hb[h] = bf16_bits(hi);
+                    lb[h] = bf16_bits(lo);
+                }
+                hw[e >> 1] = uint32_t(hb[0]) | (uint32_t(hb[1]) << 16);
+                lw[e >> 1] = uint32_t(lb[0]) | (uint32_t(lb[1]) << 16);
+            }
+            const uint32_t off = uint32_t((nrow & 7) * 16 + q8 * 128 + (nrow >> 3) * 2048);
+            *reinterpret_cast<uint4 *>(sBh + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+            *reinterpret_cast<uint4 *>(sBl + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+        }
+        // generic-proxy writes -> async proxy (the tensor core reads them)
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        __syncthreads();
+        if (tid == 0 && !a.skip_mma) {
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            const uint32_t ah = smem_u32(sAh), al = smem_u32(sAl), bh = smem_u32(sBh), bl = smem_u32(sBl);
+            uint32_t acc = 0;
+#pragma unroll
+            for (int pass = 0; pass < 3; ++pass) {
+                const uint32_t aa = pass == 2 ? al : ah, bb = pass == 1 ? bl : bh;
+#pragma unroll
+                for (int s = 0; s < 8; ++s) {
+                    mma_bf16(tmem, sdesc(aa + 256u * s, 128, 2048), sdesc(bb + 256u * s, 128, 2048), acc);
+                    acc = 1;
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mbar_a)
+                         : "memory");
+        }
+        // bounded wait for the MMAs (they finish in microseconds)
+        {
+            const uint64_t t0 = globaltimer();
+            uint32_t done = 0;
+            while (!done) {
+                asm volatile(
+                    "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+                    : "=r"(done)
+                    : "r"(mbar_a), "r"(phase)
+                    : "memory");
+                if (!done && globaltimer() - t0 > uint64_t(a.timeout_ns)) {
+                    abort_flag = 1;
+                    break;
+                }
+            }
+        }
+        __syncthreads();
+        if (abort_flag) break;
+        phase ^= 1u;
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        // read D: warp w reads lanes 32 (w % 4) .. +31, columns 64 (w / 4) .. +63
+        {
+            const int row = 32 * (warp & 3) + lane;
+            const int p = row / twoD, r = row % twoD;
+            const uint32_t jrow = a.offL[r >> 1] | a.offP[p];
+            float *sXf = reinterpret_cast<float *>(sX);
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                const int c0 = 64 * (warp >> 2) + 32 * half;
+                float v[32];
+                tmem_ld32(tmem + (uint32_t(32 * (warp & 3)) << 16) + uint32_t(c0), v);
+#pragma unroll
+                for (int i = 0; i < 32; ++i) sXf[2 * (jrow | a.offN[c0 + i]) + (r & 1)] = v[i];
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+        __syncthreads();
+        // store
+        for (int c = tid; c < (1 << (kTcM - 1)); c += kTcThreads) {
+            const uint32_t j = uint32_t(c) * 2;
+            uint64_t g = base | (j & lmask);
+            for (int q = a.lc; q < kTcM; ++q) g |= uint64_t((j >> q) & 1u) << a.tile_pos[q];
+            *reinterpret_cast<float4 *>(psi + g) = *reinterpret_cast<const float4 *>(sX + j);
+        }
+        __syncthreads();
+    }
+    if (abort_flag && tid == 0) atomicExch(err, int(SV_ERR_TIMEOUT));
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTcCols) : "memory");
+    }
+}
+
+uint16_t bf16_rne_host(float f) {
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    u += 0x7FFFu + ((u >> 16) & 1u);
+    return uint16_t(u >> 16);
+}
+
+float bf16_to_float_host(uint16_t h) {
+    const uint32_t u = uint32_t(h) << 16;
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
+}
+
+}  // namespace
+
+bool fused_tc_supported(const sv_state *h) { return h->dt == SV_C64 && h->n >= kTcM; }
+
+cudaError_t launch_fused_tc(sv_state *h, int k, const int *qubits, const double *U, int skip_mma,
+                            long long timeout_ns) {
+    const int d = 1 << k, twoD = 2 * d, P = 64 / d;
+    // A = I_P (x) Ut, split into BF16 hi / lo, K-major no-swizzle layout
+    static thread_local std::vector<uint16_t> host;
+    host.assign(2 * 128 * 128, 0);
+    for (int m = 0; m < 128; ++m)
+        for (int kk = 0; kk < 128; ++kk) {
+            double v = 0.0;
+            if (m / twoD == kk / twoD) {
+                const int rr = (m % twoD) >> 1, ar = m & 1, cc = (kk % twoD) >> 1, bc = kk & 1;
+                const double ure = U[2 * (rr * d + cc)], uim = U[2 * (rr * d + cc) + 1];
+                v = (ar == bc) ? ure : (ar == 0 ? -uim : uim);
+            }
+            const uint16_t hi = bf16_rne_host(float(v));
+            const uint16_t lo = bf16_rne_host(float(v - double(bf16_to_float_host(hi))));
+            const size_t off = size_t((m % 8) * 8 + (kk % 8) + (kk / 8) * 64 + (m / 8) * 1024);  // in elements
+            host[off] = hi;
+            host[128 * 128 + off] = lo;
+        }
+    if (!h->d_mat) {
+        cudaError_t e = cudaMalloc(&h->d_mat, 64 * 1024);
+        if (e != cudaSuccess) return e;
+    }
+    if (!h->d_err) {
+        cudaError_t e = cudaMalloc(&h->d_err, sizeof(int));
+        if (e == cudaSuccess) e = cudaMemset(h->d_err, 0, sizeof(int));
+        if (e != cudaSuccess) return e;
+    }
+    cudaError_t e = cudaMemcpyAsync(h->d_mat, host.data(), 64 * 1024, cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) return e;
+
+    TcArgs a{};
+    a.n = h->n;
+    a.k = k;
+    a.P = P;
+    a.skip_mma = skip_mma;
+    a.timeout_ns = timeout_ns;
+    // tile qubits: the block qubits plus the lowest other qubits
+    uint64_t T = 0;
+    for (int j = 0; j < k; ++j) T |= uint64_t(1) << qubits[j];
+    for (int q = 0; q < h->n && __builtin_popcountll(T) < kTcM; ++q) T |= uint64_t(1) << q;
+    int tpos_of[64];
+    {
+        int t = 0, o = 0;
+        for (int q = 0; q < h->n; ++q) {
+            if (T >> q & 1) {
+                tpos_of[q] = t;
+                a.tile_pos[t++] = uint8_t(q);
+            } else {
+                tpos_of[q] = -1;
+                a.outer_pos[o++] = uint8_t(q);
+            }
+        }
+        a.nouter = o;
+        int lc = 0;
+        while (lc < kTcM && a.tile_pos[lc] == lc) ++lc;
+        a.lc = lc;
+    }
+    for (int l = 0; l < d; ++l) {
+        uint32_t o = 0;
+        for (int j = 0; j < k; ++j)
+            if (l >> j & 1) o |= 1u << tpos_of[qubits[j]];
+        a.offL[l] = uint16_t(o);
+    }
+    // group bits: the non-block tile bits ascending; the low log2(P) of them are the pack index
+    int gbits[kTcM], ng = 0;
+    for (int t = 0; t < kTcM; ++t) {
+        bool blk = false;
+        for (int j = 0; j < k; ++j) blk |= tpos_of[qubits[j]] == t;
+        if (!blk) gbits[ng++] = t;
+    }
+    const int plog = 6 - k;
+    for (int p = 0; p < P; ++p) {
+        uint32_t o = 0;
+        for (int i = 0; i < plog; ++i)
+            if (p >> i & 1) o |= 1u << gbits[i];
+        a.offP[p] = uint16_t(o);
+    }
+    for (int nn = 0; nn < 128; ++nn) {
+        uint32_t o = 0;
+        for (int i = 0; i < 7; ++i)
+            if (nn >> i & 1) o |= 1u << gbits[plog + i];
+        a.offN[nn] = uint16_t(o);
+    }
+    a.ntiles = uint64_t(1) << (h->n - kTcM);
+    const size_t smem = 4 * size_t(kOpBytes) + (size_t(1) << kTcM) * sizeof(float2);
+    static bool configured = false;
+    if (!configured) {
+        e = cudaFuncSetAttribute(k_fused_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    int sms = 0;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+    if (e != cudaSuccess) return e;
+    const uint64_t grid = a.ntiles < uint64_t(sms) ? a.ntiles : uint64_t(sms);
+    k_fused_tc<<<unsigned(grid), kTcThreads, smem, h->stream>>>(static_cast<float2 *>(h->data),
+                                                                static_cast<const uint4 *>(h->d_mat), h->d_err, a);
+    return cudaGetLastError();
+}
+
+}  // namespace sv

@@ -11,8 +11,14 @@ namespace sv {
 constexpr int kMaxFusedQubits = 6;
 
 // Dense k-qubit block (sv_apply_fused); U is 2^k x 2^k complex row-major on
-// the host, copied into handle scratch before the launch.
+// the host, copied into handle scratch before the launch.  complex64 states
+// of at least one 2^13 tile run on the tensor cores (launch_fused_tc), the
+// rest on the CUDA cores.
 cudaError_t launch_fused(sv_state *h, int k, const int *qubits, const double *U);
+bool fused_tc_supported(const sv_state *h);
+// skip_mma != 0 never issues the MMA so the bounded wait runs out (test hook).
+cudaError_t launch_fused_tc(sv_state *h, int k, const int *qubits, const double *U, int skip_mma,
+                            long long timeout_ns);
 
 // Algorithmic HBM bytes of one per-gate update (what the method must move:
 // read + write of every amplitude the update changes).

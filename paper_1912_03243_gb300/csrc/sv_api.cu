@@ -56,6 +56,23 @@ sv_status sync_stream(cudaStream_t st, const char *what) {
 
 namespace {
 
+// After a successful synchronisation: report (and clear) a bounded device
+// wait that gave up.
+sv_status check_device_error(sv_state *h) {
+    if (!h->d_err) return SV_OK;
+    int v = 0;
+    SV_CUDA_TRY(cudaMemcpy(&v, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (v == 0) return SV_OK;
+    SV_CUDA_TRY(cudaMemset(h->d_err, 0, sizeof(int)));
+    set_error("a device-side wait timed out (tensor-core block); the state is undefined");
+    return sv_status(v);
+}
+
+sv_status sync_handle(sv_state *h, const char *what) {
+    sv_status s = sync_stream(h->stream, what);
+    return s ? s : check_device_error(h);
+}
+
 sv_status check_handle(sv_handle h) {
     if (!h) {
         set_error("NULL handle");
@@ -213,6 +230,7 @@ sv_status sv_free(sv_handle h) {
     if (h->d_idx) cudaFree(h->d_idx);
     if (h->d_amps) cudaFree(h->d_amps);
     if (h->d_mat) cudaFree(h->d_mat);
+    if (h->d_err) cudaFree(h->d_err);
     delete h;
     return SV_OK;
 }
@@ -230,7 +248,7 @@ sv_status sv_set_basis(sv_handle h, uint64_t idx) {
 sv_status sv_sync(sv_handle h) {
     sv_status s = check_handle(h);
     if (s) return s;
-    return sync_stream(h->stream, "sv_sync");
+    return sync_handle(h, "sv_sync");
 }
 
 sv_status sv_apply_gate(sv_handle h, int target, int control, const double *U) {
@@ -327,7 +345,7 @@ sv_status sv_get_codes(sv_handle h, int8_t *codes, float *scales) {
         set_error("sv_get_codes needs an SV_ENC2B state");
         return SV_ERR_DTYPE;
     }
-    s = sync_stream(h->stream, "sv_get_codes");
+    s = sync_handle(h, "sv_get_codes");
     if (s) return s;
     const size_t amps = size_t(1) << h->n;
     const size_t nb = h->n < kEncBlockLog2 ? 1 : amps >> kEncBlockLog2;
@@ -357,7 +375,7 @@ sv_status sv_amplitudes(sv_handle h, size_t m, const uint64_t *idx, double *out)
                      "sv_amplitudes");
     if (s) return s;
     SV_CUDA_TRY(cudaMemcpyAsync(out, h->d_amps, 2 * m * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-    return sync_stream(h->stream, "sv_amplitudes");
+    return sync_handle(h, "sv_amplitudes");
 }
 
 sv_status sv_norm(sv_handle h, double *out) {
@@ -371,7 +389,7 @@ sv_status sv_norm(sv_handle h, double *out) {
     s = check_launch(h->dt == SV_ENC2B ? launch_enc_norm(h, d_out) : launch_norm(h, d_out), "sv_norm");
     if (s) return s;
     SV_CUDA_TRY(cudaMemcpyAsync(out, d_out, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-    return sync_stream(h->stream, "sv_norm");
+    return sync_handle(h, "sv_norm");
 }
 
 sv_status sv_copy_to_host(sv_handle h, void *dst, size_t bytes) {
@@ -382,7 +400,7 @@ sv_status sv_copy_to_host(sv_handle h, void *dst, size_t bytes) {
         return SV_ERR_ARG;
     }
     SV_CUDA_TRY(cudaMemcpyAsync(dst, h->data, bytes, cudaMemcpyDeviceToHost, h->stream));
-    return sync_stream(h->stream, "sv_copy_to_host");
+    return sync_handle(h, "sv_copy_to_host");
 }
 
 sv_status sv_copy_from_host(sv_handle h, const void *src, size_t bytes) {
@@ -393,7 +411,7 @@ sv_status sv_copy_from_host(sv_handle h, const void *src, size_t bytes) {
         return SV_ERR_ARG;
     }
     SV_CUDA_TRY(cudaMemcpyAsync(h->data, src, bytes, cudaMemcpyHostToDevice, h->stream));
-    return sync_stream(h->stream, "sv_copy_from_host");
+    return sync_handle(h, "sv_copy_from_host");
 }
 
 int sv_gate_matrix(const char *name, const double *params, int n_params, double *out) {

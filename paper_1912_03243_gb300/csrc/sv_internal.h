@@ -89,6 +89,7 @@ struct sv_state {
     double *d_amps = nullptr;      // gathered amplitudes
     size_t gather_cap = 0;
     void *d_mat = nullptr;         // fused-gate matrix upload (64 KB)
+    int *d_err = nullptr;          // device error word (bounded waits that gave up)
     int live_plans = 0;
 };
 

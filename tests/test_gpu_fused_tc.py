@@ -1,0 +1,125 @@
+"""Dense k-qubit blocks on the tensor cores (complex64, 3 x BF16 split
+products, FP32 accumulation) against the oracle's k-qubit update, with the
+complex64 tolerances (1 - F <= 1e-5, max |d amp| <= 1e-6 ||psi||); and the
+bounded-wait failure path."""
+
+import math
+
+import numpy as np
+import pytest
+
+from paper_1912_03243_gb300 import circuits as C
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def S():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1912_03243_gb300 import build, sv
+
+    build.build()
+    sv.lib()
+    return sv
+
+
+def random_u(rng, d):
+    z = rng.normal(size=(d, d)) + 1j * rng.normal(size=(d, d))
+    q, r = np.linalg.qr(z)
+    return q * (np.diag(r) / np.abs(np.diag(r)))
+
+
+def check_c64(got, ref):
+    got = np.asarray(got, dtype=np.complex128)
+    nrm = math.sqrt(np.vdot(ref, ref).real)
+    assert np.max(np.abs(got - ref)) <= 1e-6 * nrm
+    f = abs(np.vdot(ref, got)) ** 2 / (np.vdot(ref, ref).real * np.vdot(got, got).real)
+    assert 1 - f <= 1e-5
+
+
+QUBIT_SETS = {
+    1: [[0], [7], [13]],
+    2: [[0, 1], [12, 3], [9, 5]],
+    3: [[0, 1, 2], [13, 11, 12], [4, 0, 9]],
+    4: [[0, 1, 2, 3], [10, 11, 12, 13], [8, 1, 12, 5]],
+    5: [[0, 1, 2, 3, 4], [9, 10, 11, 12, 13], [13, 0, 6, 2, 11]],
+    6: [[0, 1, 2, 3, 4, 5], [8, 9, 10, 11, 12, 13], [1, 12, 4, 9, 0, 7]],
+}
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5, 6])
+def test_blocks_14q(S, orc, k):
+    n = 14
+    rng = np.random.default_rng(100 + k)
+    psi0 = C.random_state(n, k)
+    s = S.StateVector(n, "c64")
+    for qs in QUBIT_SETS[k]:
+        u = random_u(rng, 1 << k)
+        s.from_numpy(psi0)
+        s.apply_fused(qs, u)
+        check_c64(s.to_numpy(), orc.apply_kq(psi0, qs, u))
+
+
+@pytest.mark.parametrize("n", [13, 20])
+def test_blocks_one_and_many_tiles(S, orc, n):
+    """n = 13 is a single tile; n = 20 gives 128 tiles, so persistent CTAs
+    loop over several tiles (mbarrier phases alternate)."""
+    rng = np.random.default_rng(n)
+    psi0 = C.random_state(n, 7 + n)
+    s = S.StateVector(n, "c64")
+    for k in (2, 4, 6):
+        qs = [int(q) for q in rng.choice(n, size=k, replace=False)]
+        u = random_u(rng, 1 << k)
+        s.from_numpy(psi0)
+        s.apply_fused(qs, u)
+        check_c64(s.to_numpy(), orc.apply_kq(psi0, qs, u))
+
+
+def test_block_sequence(S, orc):
+    """A sequence of dense 5-qubit blocks (each the oracle's dense matrix of
+    one window's gates) applied on the tensor cores equals the oracle
+    applying the same blocks, at 16 qubits."""
+    n = 16
+    c = C.random_circuit(n, 4, 3)
+    windows = [list(range(lo, min(lo + 5, n))) for lo in range(0, n, 5)]
+    s = S.StateVector(n, "c64")
+    ref = orc.basis_state(n)
+    for _ in range(2):
+        for qs in windows:
+            sub = C.Circuit(len(qs))
+            for name, gq, ps in c.gates:
+                if all(q in qs for q in gq):
+                    sub.add(name, *[qs.index(q) for q in gq], params=ps)
+            u = orc.dense(sub)
+            s.apply_fused(qs, u)
+            ref = orc.apply_kq(ref, qs, u)
+        for a in (4, 9, 14):
+            one = C.Circuit(n)
+            one.add("CZ", a, a + 1)
+            one.add("H", a + 1)
+            s.run(one, "pergate")
+            ref = orc.run(one, psi=ref)
+    check_c64(s.to_numpy(), ref)
+
+
+def test_timeout_path_reports_and_recovers(S, monkeypatch):
+    """The tensor-core kernel's only wait (for its MMAs) is bounded by the
+    global timer.  With the host-side hook the MMAs are never issued, the
+    wait runs out after 1 ms, the kernel releases its tensor memory and sets
+    the error word; the next synchronising call reports SV_ERR_TIMEOUT and
+    the context stays usable."""
+    n = 14
+    s = S.StateVector(n, "c64")
+    monkeypatch.setenv("SV_FAULT_INJECT", "tc_wait")
+    s.apply_fused([0, 1], np.eye(4))
+    with pytest.raises(S.SVError) as e:
+        s.sync()
+    assert e.value.status == 5
+    monkeypatch.delenv("SV_FAULT_INJECT")
+    s.set_basis(3)
+    s.apply_fused([0, 1], np.eye(4)[[1, 0, 3, 2]])  # X on qubit 0
+    a = s.amplitudes([2, 3])
+    assert abs(a[0] - 1) < 1e-6 and abs(a[1]) < 1e-6
