@@ -44,7 +44,8 @@ def parse_args():
     ap.add_argument("--n", type=int, default=32)
     ap.add_argument("--depth", type=int, default=24)
     ap.add_argument("--seed", type=int, default=1)
-    ap.add_argument("--compare-steps", type=int, default=1, help="steps of the per-gate path timed for comparison")
+    ap.add_argument("--compare-steps", type=int, default=1,
+                    help="steps of each other mode (per-gate, fused) timed for comparison")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -287,7 +288,7 @@ def time_plan(S, state, plan, steps, warmup, world, with_events=True):
 
 
 def best_mode(S, state, circ):
-    for mode in ("fused", "tiled", "pergate"):
+    for mode in ("tiled", "fused", "pergate"):
         try:
             p = state.plan(circ, mode)
             return mode, p
@@ -348,18 +349,33 @@ def run_ours(args, world, rank, local):
     plan.execute()
     inv.execute()
     a0 = state.amplitudes([0])[0]
-    roundtrip_infidelity = 1.0 - abs(a0) ** 2
+    nrm = state.norm()
+    roundtrip_infidelity = 1.0 - abs(a0) ** 2 / nrm
+    norm_drift = nrm - 1.0
     inv.free()
 
-    # comparison: the plain per-gate path on the same workload
-    compare = None
-    if mode != "pergate" and args.compare_steps > 0:
-        pg = state.plan(circ, "pergate")
+    # comparison: the other modes on the same workload (fused k-qubit blocks on
+    # the tensor cores; the plain per-gate path)
+    compare = {}
+    for other in ("fused", "pergate"):
+        if other == mode or args.compare_steps <= 0:
+            continue
+        pg = state.plan(circ, other)
         tp, _ = time_plan(S, state, pg, args.compare_steps, 1, world, with_events=False)
-        compare = {"mode": "pergate", "gates_per_s": pg.gates * args.compare_steps * world / tp,
-                   "gbs": pg.bytes * args.compare_steps * world / tp / 1e9, "launches_per_step": pg.passes,
-                   "ms_per_step": 1e3 * tp / args.compare_steps,
-                   "layers_per_s": args.depth * args.compare_steps * world / tp}
+        kernels = sorted({k for k, _ in pg.launch_info()})
+        compare[other] = {"gates_per_s": pg.gates * args.compare_steps * world / tp,
+                          "gbs": pg.bytes * args.compare_steps * world / tp / 1e9, "launches_per_step": pg.passes,
+                          "ms_per_step": 1e3 * tp / args.compare_steps,
+                          "layers_per_s": args.depth * args.compare_steps * world / tp,
+                          "kernels": kernels[:4]}
+        if other == "fused":
+            state.set_basis(0)
+            pg.execute()
+            inv = state.plan(C.inverse_circuit(circ), other)
+            inv.execute()
+            a0 = state.amplitudes([0])[0]
+            compare[other]["roundtrip_1_minus_fidelity"] = 1.0 - abs(a0) ** 2 / state.norm()
+            inv.free()
         pg.free()
 
     # end to end through the C ABI with host buffers: circuit text in, 1024
@@ -396,7 +412,8 @@ def run_ours(args, world, rank, local):
                        "mode": mode, "launches_per_step": launches_per_step, "parallelism": f"replicas x{world}",
                        "l2": "state (32 GiB) larger than L2, no flush"},
             "hbm_gbs": gbs, "layers_per_s": args.depth * args.steps * world / t,
-            "accuracy": {"roundtrip_1_minus_fidelity": roundtrip_infidelity},
+            "accuracy": {"roundtrip_1_minus_fidelity": roundtrip_infidelity, "roundtrip_norm_minus_1": norm_drift,
+                         "note": "circuit then its inverse from |0...0>; fidelity = |<0|psi>|^2 / ||psi||^2"},
             "compare": compare, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": args.steps * (launches_per_step + 1),
         }

@@ -1,0 +1,34 @@
+// Tensor-core dense k-qubit blocks (k_fused_tc.cu): launch arguments shared
+// with the plan code, which prepares every block of a fused plan once.
+#pragma once
+
+#include <cstdint>
+
+#include "sv_internal.h"
+
+namespace sv {
+
+constexpr int kTcM = 13;                            // tile bits (2^13 amplitudes per tile)
+constexpr size_t kTcOperandBytes = 2 * 128 * 128 * 2;  // A hi + A lo, BF16 (64 KiB)
+
+struct TcArgs {
+    int n, k, P;
+    int nouter;
+    int lc;
+    uint64_t ntiles;
+    long long timeout_ns;
+    int skip_mma;                 // test hook: never issue the MMA (the wait must time out)
+    uint8_t tile_pos[kTcM];
+    uint8_t outer_pos[40];
+    uint16_t offL[64];            // tile index offset of block-local index l
+    uint16_t offP[64];            // tile index offset of pack p
+    uint16_t offN[128];           // tile index offset of column n
+};
+
+// Build the BF16 hi/lo operand image of block U (a_ops: 2 * 128 * 128
+// elements) and the launch arguments for an n-qubit state.
+void tc_prepare(int n, int k, const int *qubits, const double *U, uint16_t *a_ops, TcArgs *args);
+// Launch with operands already in device memory (dA: kTcOperandBytes).
+cudaError_t tc_launch(sv_state *h, const TcArgs &args, const void *dA);
+
+}  // namespace sv

@@ -82,10 +82,7 @@ __global__ void __launch_bounds__(kThreads) k_fused_dense(C2<R> *__restrict__ ps
 }  // namespace
 
 cudaError_t launch_fused(sv_state *h, int k, const int *qubits, const double *U) {
-    if (fused_tc_supported(h)) {
-        const bool hook = fault_injected("tc_wait");
-        return launch_fused_tc(h, k, qubits, U, hook ? 1 : 0, hook ? 1000000LL : 2000000000LL);
-    }
+    if (fused_tc_supported(h)) return launch_fused_tc(h, k, qubits, U);
     const int d = 1 << k;
     if (!h->d_mat) {
         cudaError_t e = cudaMalloc(&h->d_mat, sizeof(C2<double>) << (2 * kMaxFusedQubits));

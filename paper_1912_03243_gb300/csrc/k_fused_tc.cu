@@ -29,29 +29,15 @@
 #include <cstring>
 #include <vector>
 
+#include "fused_tc.h"
 #include "plan.h"
 
 namespace sv {
 namespace {
 
-constexpr int kTcM = 13;          // tile bits
 constexpr int kTcThreads = 256;
 constexpr int kTcCols = 128;      // TMEM columns of the accumulator (N)
 constexpr uint32_t kOpBytes = 128 * 128 * 2;  // one BF16 operand (32 KiB)
-
-struct TcArgs {
-    int n, k, P;
-    int nouter;
-    int lc;
-    uint64_t ntiles;
-    long long timeout_ns;
-    int skip_mma;                 // test hook: never issue the MMA (the wait must time out)
-    uint8_t tile_pos[kTcM];
-    uint8_t outer_pos[40];
-    uint16_t offL[64];            // tile index offset of block-local index l
-    uint16_t offP[64];            // tile index offset of pack p
-    uint16_t offN[128];           // tile index offset of column n
-};
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return uint32_t(__cvta_generic_to_shared(p)); }
 
@@ -271,12 +257,10 @@ float bf16_to_float_host(uint16_t h) {
 
 bool fused_tc_supported(const sv_state *h) { return h->dt == SV_C64 && h->n >= kTcM; }
 
-cudaError_t launch_fused_tc(sv_state *h, int k, const int *qubits, const double *U, int skip_mma,
-                            long long timeout_ns) {
+void tc_prepare(int n, int k, const int *qubits, const double *U, uint16_t *a_ops, TcArgs *args) {
     const int d = 1 << k, twoD = 2 * d, P = 64 / d;
     // A = I_P (x) Ut, split into BF16 hi / lo, K-major no-swizzle layout
-    static thread_local std::vector<uint16_t> host;
-    host.assign(2 * 128 * 128, 0);
+    for (int i = 0; i < 2 * 128 * 128; ++i) a_ops[i] = 0;
     for (int m = 0; m < 128; ++m)
         for (int kk = 0; kk < 128; ++kk) {
             double v = 0.0;
@@ -288,89 +272,102 @@ cudaError_t launch_fused_tc(sv_state *h, int k, const int *qubits, const double 
             const uint16_t hi = bf16_rne_host(float(v));
             const uint16_t lo = bf16_rne_host(float(v - double(bf16_to_float_host(hi))));
             const size_t off = size_t((m % 8) * 8 + (kk % 8) + (kk / 8) * 64 + (m / 8) * 1024);  // in elements
-            host[off] = hi;
-            host[128 * 128 + off] = lo;
+            a_ops[off] = hi;
+            a_ops[128 * 128 + off] = lo;
         }
-    if (!h->d_mat) {
-        cudaError_t e = cudaMalloc(&h->d_mat, 64 * 1024);
-        if (e != cudaSuccess) return e;
+    TcArgs &a = *args;
+    a = TcArgs{};
+    a.n = n;
+    a.k = k;
+    a.P = P;
+    // tile qubits: the block qubits plus the lowest other qubits
+    uint64_t T = 0;
+    for (int j = 0; j < k; ++j) T |= uint64_t(1) << qubits[j];
+    for (int q = 0; q < n && __builtin_popcountll(T) < kTcM; ++q) T |= uint64_t(1) << q;
+    int tpos_of[64];
+    int t = 0, o = 0;
+    for (int q = 0; q < n; ++q) {
+        if (T >> q & 1) {
+            tpos_of[q] = t;
+            a.tile_pos[t++] = uint8_t(q);
+        } else {
+            tpos_of[q] = -1;
+            a.outer_pos[o++] = uint8_t(q);
+        }
+    }
+    a.nouter = o;
+    int lc = 0;
+    while (lc < kTcM && a.tile_pos[lc] == lc) ++lc;
+    a.lc = lc;
+    for (int l = 0; l < d; ++l) {
+        uint32_t off = 0;
+        for (int j = 0; j < k; ++j)
+            if (l >> j & 1) off |= 1u << tpos_of[qubits[j]];
+        a.offL[l] = uint16_t(off);
+    }
+    // group bits: the non-block tile bits ascending; the low log2(P) of them are the pack index
+    int gbits[kTcM], ng = 0;
+    for (int tb = 0; tb < kTcM; ++tb) {
+        bool blk = false;
+        for (int j = 0; j < k; ++j) blk |= tpos_of[qubits[j]] == tb;
+        if (!blk) gbits[ng++] = tb;
+    }
+    const int plog = 6 - k;
+    for (int p = 0; p < P; ++p) {
+        uint32_t off = 0;
+        for (int i = 0; i < plog; ++i)
+            if (p >> i & 1) off |= 1u << gbits[i];
+        a.offP[p] = uint16_t(off);
+    }
+    for (int nn = 0; nn < 128; ++nn) {
+        uint32_t off = 0;
+        for (int i = 0; i < 7; ++i)
+            if (nn >> i & 1) off |= 1u << gbits[plog + i];
+        a.offN[nn] = uint16_t(off);
+    }
+    a.ntiles = uint64_t(1) << (n - kTcM);
+    a.timeout_ns = 2000000000LL;
+}
+
+cudaError_t tc_launch(sv_state *h, const TcArgs &args, const void *dA) {
+    TcArgs a = args;
+    if (fault_injected("tc_wait")) {  // test hook: the MMA wait runs out
+        a.skip_mma = 1;
+        a.timeout_ns = 1000000LL;
     }
     if (!h->d_err) {
         cudaError_t e = cudaMalloc(&h->d_err, sizeof(int));
         if (e == cudaSuccess) e = cudaMemset(h->d_err, 0, sizeof(int));
         if (e != cudaSuccess) return e;
     }
-    cudaError_t e = cudaMemcpyAsync(h->d_mat, host.data(), 64 * 1024, cudaMemcpyHostToDevice, h->stream);
-    if (e != cudaSuccess) return e;
-
-    TcArgs a{};
-    a.n = h->n;
-    a.k = k;
-    a.P = P;
-    a.skip_mma = skip_mma;
-    a.timeout_ns = timeout_ns;
-    // tile qubits: the block qubits plus the lowest other qubits
-    uint64_t T = 0;
-    for (int j = 0; j < k; ++j) T |= uint64_t(1) << qubits[j];
-    for (int q = 0; q < h->n && __builtin_popcountll(T) < kTcM; ++q) T |= uint64_t(1) << q;
-    int tpos_of[64];
-    {
-        int t = 0, o = 0;
-        for (int q = 0; q < h->n; ++q) {
-            if (T >> q & 1) {
-                tpos_of[q] = t;
-                a.tile_pos[t++] = uint8_t(q);
-            } else {
-                tpos_of[q] = -1;
-                a.outer_pos[o++] = uint8_t(q);
-            }
-        }
-        a.nouter = o;
-        int lc = 0;
-        while (lc < kTcM && a.tile_pos[lc] == lc) ++lc;
-        a.lc = lc;
-    }
-    for (int l = 0; l < d; ++l) {
-        uint32_t o = 0;
-        for (int j = 0; j < k; ++j)
-            if (l >> j & 1) o |= 1u << tpos_of[qubits[j]];
-        a.offL[l] = uint16_t(o);
-    }
-    // group bits: the non-block tile bits ascending; the low log2(P) of them are the pack index
-    int gbits[kTcM], ng = 0;
-    for (int t = 0; t < kTcM; ++t) {
-        bool blk = false;
-        for (int j = 0; j < k; ++j) blk |= tpos_of[qubits[j]] == t;
-        if (!blk) gbits[ng++] = t;
-    }
-    const int plog = 6 - k;
-    for (int p = 0; p < P; ++p) {
-        uint32_t o = 0;
-        for (int i = 0; i < plog; ++i)
-            if (p >> i & 1) o |= 1u << gbits[i];
-        a.offP[p] = uint16_t(o);
-    }
-    for (int nn = 0; nn < 128; ++nn) {
-        uint32_t o = 0;
-        for (int i = 0; i < 7; ++i)
-            if (nn >> i & 1) o |= 1u << gbits[plog + i];
-        a.offN[nn] = uint16_t(o);
-    }
-    a.ntiles = uint64_t(1) << (h->n - kTcM);
     const size_t smem = 4 * size_t(kOpBytes) + (size_t(1) << kTcM) * sizeof(float2);
     static bool configured = false;
     if (!configured) {
-        e = cudaFuncSetAttribute(k_fused_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        const cudaError_t e = cudaFuncSetAttribute(k_fused_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
         if (e != cudaSuccess) return e;
         configured = true;
     }
     int sms = 0;
-    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+    const cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
     if (e != cudaSuccess) return e;
     const uint64_t grid = a.ntiles < uint64_t(sms) ? a.ntiles : uint64_t(sms);
     k_fused_tc<<<unsigned(grid), kTcThreads, smem, h->stream>>>(static_cast<float2 *>(h->data),
-                                                                static_cast<const uint4 *>(h->d_mat), h->d_err, a);
+                                                                static_cast<const uint4 *>(dA), h->d_err, a);
     return cudaGetLastError();
+}
+
+cudaError_t launch_fused_tc(sv_state *h, int k, const int *qubits, const double *U) {
+    static thread_local std::vector<uint16_t> host;
+    host.resize(2 * 128 * 128);
+    TcArgs a;
+    tc_prepare(h->n, k, qubits, U, host.data(), &a);
+    if (!h->d_mat) {
+        const cudaError_t e = cudaMalloc(&h->d_mat, kTcOperandBytes);
+        if (e != cudaSuccess) return e;
+    }
+    const cudaError_t e = cudaMemcpyAsync(h->d_mat, host.data(), kTcOperandBytes, cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) return e;
+    return tc_launch(h, a, h->d_mat);
 }
 
 }  // namespace sv

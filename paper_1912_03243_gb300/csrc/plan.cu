@@ -20,7 +20,42 @@ double gate1_bytes(const sv_state *h, const Gate1 &g) {
 
 namespace {
 
-void destroy_plan(sv_plan_s *p) { delete p; }
+void destroy_plan(sv_plan_s *p) {
+    if (p->d_tcA) cudaFree(p->d_tcA);
+    delete p;
+}
+
+// Fused mode: blocks of at most k qubits; the autotuner takes the k in 3..6
+// with the fewest blocks (each block is one HBM pass; ties to the smaller k).
+sv_status build_fused_plan(sv_state *h, const Circuit &c, sv_plan_s *p) {
+    std::vector<FusedBlock> best;
+    int bestk = 0;
+    const int kmin = h->n < 3 ? h->n : 3;
+    for (int k = kmin; k <= kMaxFusedQubits && k <= h->n; ++k) {
+        std::vector<FusedBlock> b = fuse_blocks(c, k);
+        if (bestk == 0 || b.size() < best.size()) {
+            best.swap(b);
+            bestk = k;
+        }
+    }
+    p->fused_k = bestk;
+    const double pass_bytes = 2.0 * double(uint64_t(1) << h->n) * (h->dt == SV_C64 ? 8.0 : 16.0);
+    if (fused_tc_supported(h) && !best.empty()) {
+        std::vector<uint16_t> img(best.size() * (kTcOperandBytes / 2));
+        p->tcargs.resize(best.size());
+        for (size_t i = 0; i < best.size(); ++i)
+            tc_prepare(h->n, best[i].k, best[i].qubits, best[i].U.data(), img.data() + i * (kTcOperandBytes / 2),
+                       &p->tcargs[i]);
+        SV_CUDA_TRY(cudaMalloc(&p->d_tcA, img.size() * 2));
+        SV_CUDA_TRY(cudaMemcpy(p->d_tcA, img.data(), img.size() * 2, cudaMemcpyHostToDevice));
+        for (size_t i = 0; i < best.size(); ++i) p->launches.push_back(PlanLaunch{2, int(i), pass_bytes});
+    } else {
+        p->blocks.swap(best);
+        for (size_t i = 0; i < p->blocks.size(); ++i) p->launches.push_back(PlanLaunch{3, int(i), pass_bytes});
+    }
+    p->bytes = pass_bytes * double(p->launches.size());
+    return SV_OK;
+}
 
 template <typename R>
 sv_status upload_tile_plan(sv_plan_s *p, const TilePlan<R> &tp) {
@@ -47,11 +82,22 @@ sv_status build_tile_plan(sv_state *h, const Circuit &c, sv_plan_s *p) {
 
 cudaError_t launch_one(sv_plan_s *p, const PlanLaunch &l) {
     if (l.kind == 0) return launch_gate1(p->h, p->pergate[size_t(l.index)]);
+    if (l.kind == 2)
+        return tc_launch(p->h, p->tcargs[size_t(l.index)],
+                         static_cast<const char *>(p->d_tcA) + size_t(l.index) * kTcOperandBytes);
+    if (l.kind == 3) {
+        const FusedBlock &b = p->blocks[size_t(l.index)];
+        return launch_fused(p->h, b.k, b.qubits, b.U.data());
+    }
     return launch_jit_pass(p->h, p->tfns[size_t(l.index)], p->h->n);
 }
 
 const char *launch_name(const sv_plan_s *p, const PlanLaunch &l) {
     if (l.kind == 0) return gate1_kernel_name(p->h, p->pergate[size_t(l.index)]);
+    static const char *tc_names[] = {"k_fused_tc<k=0>", "k_fused_tc<k=1>", "k_fused_tc<k=2>", "k_fused_tc<k=3>",
+                                     "k_fused_tc<k=4>", "k_fused_tc<k=5>", "k_fused_tc<k=6>"};
+    if (l.kind == 2) return tc_names[p->tcargs[size_t(l.index)].k];
+    if (l.kind == 3) return p->h->dt == SV_C64 ? "k_fused_dense<f32>" : "k_fused_dense<f64>";
     return tile_kernel_name(p->h);
 }
 
@@ -90,11 +136,12 @@ sv_status sv_plan_create(sv_handle h, const char *text, int mode, sv_plan *out) 
     p->gates = int64_t(c.instrs.size());
     const int tile_m = h->dt == SV_C64 ? kTileM64 : kTileM128;
     if (mode == SV_MODE_FUSED) {
-        delete p;
-        set_error("mode %d is not available yet", mode);
-        return SV_ERR_UNSUPPORTED;
-    }
-    if (mode == SV_MODE_PERGATE || h->n < tile_m) {
+        s = build_fused_plan(h, c, p);
+        if (s) {
+            destroy_plan(p);
+            return s;
+        }
+    } else if (mode == SV_MODE_PERGATE || h->n < tile_m) {
         // per-gate updates (also the tiled mode's path for states smaller than one tile)
         p->pergate = lower_to_gate1(c);
         for (size_t i = 0; i < p->pergate.size(); ++i) {

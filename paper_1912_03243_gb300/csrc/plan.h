@@ -3,6 +3,7 @@
 
 #include <vector>
 
+#include "fused_tc.h"
 #include "sv_internal.h"
 #include "tile.h"
 
@@ -16,9 +17,20 @@ constexpr int kMaxFusedQubits = 6;
 // rest on the CUDA cores.
 cudaError_t launch_fused(sv_state *h, int k, const int *qubits, const double *U);
 bool fused_tc_supported(const sv_state *h);
-// skip_mma != 0 never issues the MMA so the bounded wait runs out (test hook).
-cudaError_t launch_fused_tc(sv_state *h, int k, const int *qubits, const double *U, int skip_mma,
-                            long long timeout_ns);
+cudaError_t launch_fused_tc(sv_state *h, int k, const int *qubits, const double *U);
+
+// A k-qubit block of a fused plan: the ordered product of the gates it
+// absorbed, 2^k x 2^k complex row-major (re, im), local bit j <-> qubits[j].
+struct FusedBlock {
+    int k = 0;
+    int qubits[kMaxFusedQubits] = {0};
+    std::vector<double> U;
+    int gates = 0;
+};
+
+// Greedy fusion of the circuit into blocks of at most kmax qubits; gates are
+// reordered only across gates they commute with.  Returns the blocks.
+std::vector<FusedBlock> fuse_blocks(const Circuit &c, int kmax);
 
 // Algorithmic HBM bytes of one per-gate update (what the method must move:
 // read + write of every amplitude the update changes).
@@ -31,7 +43,8 @@ const char *gate1_kernel_name(const sv_state *h, const Gate1 &g);
 
 // One kernel launch of a plan.
 struct PlanLaunch {
-    int kind;      // 0: per-gate update pergate[index]; 1: compiled tile pass tfns[index]
+    int kind;      // 0: per-gate update pergate[index]; 1: compiled tile pass tfns[index];
+                   // 2: tensor-core block tcargs[index]; 3: CUDA-core block blocks[index]
     int index;
     double bytes;  // algorithmic bytes
 };
@@ -41,7 +54,11 @@ struct sv_plan_s {
     int mode = 0;
     int64_t gates = 0;                     // gates of the circuit text
     std::vector<sv::Gate1> pergate;        // per-gate updates
-    std::vector<void *> tfns;              // compiled tile passes (CUfunction)
+    std::vector<void *> tfns;              // compiled tile passes
+    std::vector<sv::FusedBlock> blocks;    // fused blocks (CUDA-core kernel)
+    std::vector<sv::TcArgs> tcargs;        // fused blocks (tensor-core kernel)
+    void *d_tcA = nullptr;                 // their operand images, kTcOperandBytes each
+    int fused_k = 0;
     std::vector<PlanLaunch> launches;      // execution order
     double bytes = 0.0;                    // algorithmic bytes of one execution
 };
