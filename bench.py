@@ -48,6 +48,8 @@ def parse_args():
                     help="steps of each other mode (per-gate, fused) timed for comparison")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the two-byte-code (35 qubits) and decomposition (48 qubits) measurements")
     return ap.parse_args()
 
 
@@ -287,6 +289,74 @@ def time_plan(S, state, plan, steps, warmup, world, with_events=True):
     return max_over_ranks(world, t), per_launch
 
 
+def dominant_roofline(info, per_launch, steps, peak, peak_kind):
+    tot, cnt, byt = {}, {}, {}
+    for k in range(steps):
+        for i, (name, b) in enumerate(info):
+            tot[name] = tot.get(name, 0.0) + per_launch[k][i]
+            cnt[name] = cnt.get(name, 0) + 1
+            byt[name] = byt.get(name, 0.0) + b
+    dom = max(tot, key=tot.get)
+    achieved = byt[dom] / (tot[dom] / 1e3) / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "kernel": dom, "launches": cnt[dom], "avg_launch_ms": tot[dom] / cnt[dom],
+            "bytes_per_launch": byt[dom] / cnt[dom], "peak_kind": peak_kind,
+            "share_of_step": tot[dom] / sum(tot.values())}
+
+
+def bench_enc2b(S, C, args, world, peak, peak_kind):
+    """Two-byte code at 35 qubits (2^35 x 2 B + 2^27 x 4 B = 64.5 GB): the
+    first layer of the depth-12 random circuit (52 gates), one
+    decode-gate-encode pass per gate."""
+    import torch
+
+    n, depth = 35, 12
+    need = S.sv_bytes_required(n, "enc2b")
+    if torch.cuda.mem_get_info()[0] < need + (8 << 30):
+        return {"skipped": "not enough device memory"}
+    circ = C.random_circuit(n, depth, args.seed)
+    layer = C.Circuit(n)
+    layer.gates = circ.gates[: n + n // 2]
+    st = S.StateVector(n, "enc2b")
+    plan = st.plan(layer, "pergate")
+    info = plan.launch_info()
+    t, per_launch = time_plan(S, st, plan, 2, 1, world)
+    out = {"workload": f"first layer ({plan.gates} gates) of the {n}-qubit depth-{depth} random circuit, "
+                       f"two-byte code ({need / 2**30:.1f} GiB)",
+           "gates_per_s": plan.gates * 2 / t, "ms_per_gate": 1e3 * t / (2 * plan.gates),
+           "gbs": plan.bytes * 2 / t / 1e9, "full_circuit_s_est": len(circ) * t / (2 * plan.gates),
+           "roofline": dominant_roofline(info, per_launch, 2, peak, peak_kind)}
+    plan.free()
+    st.free()
+    del st
+    torch.cuda.empty_cache()
+    return out
+
+
+def bench_cut(S, C):
+    """Decomposition of the 48-qubit 6x8 grid (depth 8, S = 8): 256 branches
+    x 2 halves of 2^24 amplitudes (two batched 2^32 complex64 vectors),
+    1024 output amplitudes; the second of two calls is timed (the first
+    compiles the passes)."""
+    import torch
+
+    if torch.cuda.mem_get_info()[0] < (72 << 30):
+        return {"skipped": "not enough device memory"}
+    c = C.grid_circuit(6, 8, 8, 1)
+    mask = C.grid_partition_mask(6, 8, 3)
+    z = C.random_bitstrings(1024, 48, 7)
+    S.sv_cut_amplitudes(c, 48, mask, z)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    amps, s = S.sv_cut_amplitudes(c, 48, mask, z)
+    torch.cuda.synchronize()
+    t = time.perf_counter() - t0
+    return {"workload": "6x8 grid, 48 qubits, depth 8, rows 0-2 | 3-5, projector decomposition", "cut_gates": s,
+            "branches": 1 << s, "amplitudes": int(z.size), "ms_per_call": 1e3 * t,
+            "note": "end to end: planning, allocation, both batched halves, FP64 branch sum, copy back",
+            "mean_abs2_times_2^48": float((abs(amps) ** 2).mean() * 2.0 ** 48)}
+
+
 def best_mode(S, state, circ):
     for mode in ("tiled", "fused", "pergate"):
         try:
@@ -403,6 +473,12 @@ def run_ours(args, world, rank, local):
         cpu = {"value": v, "unit": "gates/s", "cores": 1, "kind": "oracle", "sample": sdesc}
 
     plan.free()
+    extras = None
+    if rank == 0 and world == 1 and not args.no_extras and args.n == 32:
+        state.free()
+        del state
+        torch.cuda.empty_cache()
+        extras = {"enc2b_35q": bench_enc2b(S, C, args, world, hbm_peak, peak_kind), "cut_48q": bench_cut(S, C)}
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "gates/s", "n_gpus": world, "steps": args.steps,
@@ -414,7 +490,7 @@ def run_ours(args, world, rank, local):
             "hbm_gbs": gbs, "layers_per_s": args.depth * args.steps * world / t,
             "accuracy": {"roundtrip_1_minus_fidelity": roundtrip_infidelity, "roundtrip_norm_minus_1": norm_drift,
                          "note": "circuit then its inverse from |0...0>; fidelity = |<0|psi>|^2 / ||psi||^2"},
-            "compare": compare, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "compare": compare, "extras": extras, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": args.steps * (launches_per_step + 1),
         }
         print(json.dumps(line), flush=True)

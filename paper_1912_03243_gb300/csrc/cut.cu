@@ -100,7 +100,7 @@ struct Half {
 };
 
 sv_status run_half(Half &h, cudaStream_t st, int S, std::vector<void *> *fns, TilePlan<float> *tp) {
-    sv_status s = plan_tiles<float>(h.gates, h.nq, TileConfig{kTileM64, kTileRB64, kTileLow64, true}, tp);
+    sv_status s = plan_tiles<float>(h.gates, h.nq, TileConfig{kTileM64, tile_rb64(), kTileLow64, true}, tp);
     if (s) return s;
     s = jit_tile_plan(*tp, fns);
     if (s) return s;
@@ -115,7 +115,7 @@ sv_status run_half(Half &h, cudaStream_t st, int S, std::vector<void *> *fns, Ti
     s = check_launch(cudaGetLastError(), "k_branch_init");
     if (s) return s;
     for (void *fn : *fns) {
-        s = check_launch(launch_jit_pass(&tmp, fn, h.nq), "branch pass");
+        s = check_launch(launch_jit_pass(&tmp, fn, h.nq, tp->rb), "branch pass");
         if (s) return s;
     }
     tmp.data = nullptr;

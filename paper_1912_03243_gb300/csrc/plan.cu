@@ -61,6 +61,7 @@ template <typename R>
 sv_status upload_tile_plan(sv_plan_s *p, const TilePlan<R> &tp) {
     sv_status s = jit_tile_plan(tp, &p->tfns);
     if (s) return s;
+    p->tile_rb = tp.rb;
     const double pass_bytes = 2.0 * double(uint64_t(1) << p->h->n) * (p->h->dt == SV_C64 ? 8.0 : 16.0);
     for (size_t i = 0; i < tp.passes.size(); ++i) {
         p->launches.push_back(PlanLaunch{1, int(i), pass_bytes});  // compiled pass i
@@ -72,7 +73,7 @@ sv_status upload_tile_plan(sv_plan_s *p, const TilePlan<R> &tp) {
 sv_status build_tile_plan(sv_state *h, const Circuit &c, sv_plan_s *p) {
     if (h->dt == SV_C64) {
         TilePlan<float> tp;
-        sv_status s = plan_tiles<float>(c, h->n, TileConfig{kTileM64, kTileRB64, kTileLow64, true}, &tp);
+        sv_status s = plan_tiles<float>(c, h->n, TileConfig{kTileM64, tile_rb64(), kTileLow64, true}, &tp);
         return s ? s : upload_tile_plan(p, tp);
     }
     TilePlan<double> tp;
@@ -89,7 +90,7 @@ cudaError_t launch_one(sv_plan_s *p, const PlanLaunch &l) {
         const FusedBlock &b = p->blocks[size_t(l.index)];
         return launch_fused(p->h, b.k, b.qubits, b.U.data());
     }
-    return launch_jit_pass(p->h, p->tfns[size_t(l.index)], p->h->n);
+    return launch_jit_pass(p->h, p->tfns[size_t(l.index)], p->h->n, p->tile_rb);
 }
 
 const char *launch_name(const sv_plan_s *p, const PlanLaunch &l) {
@@ -238,7 +239,7 @@ sv_status sv_plan_stats(const char *text, int n, sv_dtype dt, int compile, int64
             return SV_ERR_UNSUPPORTED;
         }
         TilePlan<float> tp;
-        s = plan_tiles<float>(c, n, TileConfig{kTileM64, kTileRB64, kTileLow64, true}, &tp);
+        s = plan_tiles<float>(c, n, TileConfig{kTileM64, tile_rb64(), kTileLow64, true}, &tp);
         return s ? s : count(tp);
     }
     if (n < kTileM128) {

@@ -55,6 +55,7 @@ struct sv_plan_s {
     int64_t gates = 0;                     // gates of the circuit text
     std::vector<sv::Gate1> pergate;        // per-gate updates
     std::vector<void *> tfns;              // compiled tile passes
+    int tile_rb = 0;                       // their register bits per thread
     std::vector<sv::FusedBlock> blocks;    // fused blocks (CUDA-core kernel)
     std::vector<sv::TcArgs> tcargs;        // fused blocks (tensor-core kernel)
     void *d_tcA = nullptr;                 // their operand images, kTcOperandBytes each

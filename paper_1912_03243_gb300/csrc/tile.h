@@ -84,6 +84,7 @@ struct TileConfig {
 
 template <typename R>
 struct TilePlan {
+    int m = 0, rb = 0;  // tile bits, register bits per thread
     std::vector<TilePassArgs> passes;
     std::vector<TileOp<R>> ops;
     std::vector<TileSeg> segs;
@@ -125,8 +126,12 @@ sv_status jit_tile_plan(const TilePlan<double> &tp, std::vector<void *> *fns);
 // Compile only (no device needed): NVRTC-compiles every pass, returns status.
 sv_status jit_compile_check(const TilePlan<float> &tp);
 sv_status jit_compile_check(const TilePlan<double> &tp);
-// Launch one compiled pass over the whole state (grid = 2^(n-m) CTAs).
-cudaError_t launch_jit_pass(sv_state *h, void *fn, int n);
+// Register bits per thread of complex64 tile passes (SV_TILE_RB overrides,
+// 4 or 5).
+int tile_rb64();
+// Launch one compiled pass over the whole state (grid = 2^(n-m) CTAs of
+// 2^(m-rb) threads).
+cudaError_t launch_jit_pass(sv_state *h, void *fn, int n, int rb);
 const char *tile_kernel_name(const sv_state *h);
 
 }  // namespace sv

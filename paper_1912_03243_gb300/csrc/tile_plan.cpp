@@ -4,8 +4,10 @@
 // (Sec. 2); the planner only reorders gates that commute (gates on disjoint
 // qubits, or diagonal gates), so the result is the circuit's.
 #include <algorithm>
+#include <iterator>
 #include <cmath>
 #include <complex>
+#include <cstdlib>
 
 #include "plan.h"
 #include "tile.h"
@@ -226,11 +228,19 @@ uint64_t choose_tile(const std::vector<PGate> &G, const std::vector<int> &pendin
 
 }  // namespace
 
+int tile_rb64() {
+    const char *e = std::getenv("SV_TILE_RB");
+    const int v = e ? std::atoi(e) : kTileRB64;
+    return (v == 4 || v == 5) ? v : kTileRB64;
+}
+
 template <typename R>
 sv_status plan_tiles(const std::vector<PGate> &G, int n, const TileConfig &cfg, TilePlan<R> *out) {
     out->passes.clear();
     out->ops.clear();
     out->segs.clear();
+    out->m = cfg.m;
+    out->rb = cfg.rb;
     const int m = cfg.m, rb = cfg.rb, L = cfg.low;
     if (n < m) {
         set_error("tiled mode needs n >= %d", m);
@@ -326,16 +336,46 @@ sv_status plan_tiles(const std::vector<PGate> &G, int n, const TileConfig &cfg, 
                 const int p = (k + 1) % m;
                 Rset |= uint64_t(1) << pa.tile_pos[p];
             }
-            std::vector<int> seg_ops, rest2;
+            std::vector<int> applicable, rest2;
             bF = bD = 0;
             for (int idx : remaining) {
                 const PGate &g = G[size_t(idx)];
                 const uint64_t F = full_of(g), D = diag_of(g);
-                if (!conflicts(F, D, bF, bD) && (F & ~Rset) == 0) seg_ops.push_back(idx);
+                if (!conflicts(F, D, bF, bD) && (F & ~Rset) == 0) applicable.push_back(idx);
                 else {
                     bF |= F;
                     bD |= D;
                     rest2.push_back(idx);
+                }
+            }
+            // Diagonal gates go where they are cheapest: one is emitted now if
+            // all its qubits are register qubits here (a compile-time phase or
+            // sign), if a later non-diagonal gate of this segment acts on one
+            // of its qubits, or if no non-diagonal gate is left for later
+            // segments of the pass; otherwise it waits for a later segment.
+            bool nondiag_left = false;
+            for (int idx : rest2) nondiag_left |= G[size_t(idx)].kind == 0;
+            std::vector<int> seg_ops;
+            {
+                std::vector<char> keep(applicable.size(), 1);
+                if (nondiag_left) {
+                    uint64_t later_full = 0;
+                    for (size_t i = applicable.size(); i-- > 0;) {
+                        const PGate &g = G[size_t(applicable[i])];
+                        if (g.kind == 0) later_full |= full_of(g);
+                        else if (!(diag_of(g) & later_full) && toc(g.scale) == cd(1) && (diag_of(g) & ~Rset))
+                            keep[i] = 0;  // defer unless needed now or all its qubits are register qubits
+                    }
+                }
+                std::vector<int> deferred;
+                for (size_t i = 0; i < applicable.size(); ++i)
+                    (keep[i] ? seg_ops : deferred).push_back(applicable[i]);
+                if (!deferred.empty()) {
+                    // deferred gates go back in circuit order
+                    std::vector<int> merged;
+                    merged.reserve(deferred.size() + rest2.size());
+                    std::merge(deferred.begin(), deferred.end(), rest2.begin(), rest2.end(), std::back_inserter(merged));
+                    rest2.swap(merged);
                 }
             }
             remaining.swap(rest2);
