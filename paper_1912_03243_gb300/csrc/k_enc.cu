@@ -42,23 +42,27 @@ __device__ __forceinline__ uint64_t insert_zero(uint64_t x, int p) {
     return ((x ^ lo) << 1) | lo;
 }
 
-// Table T[k] = fl(k/127) replicated per bank: tab[k * 32 + lane].
+// Signed table, indexed by the code's byte u = (uint8)q: tab[u * 32 + lane] =
+// sign(q) fl(|q| / 127), replicated per bank.  fl(s * (-t)) = -fl(s * t), so
+// s * tab[u] is exactly sign(q) fl(s T[|q|]).
+constexpr int kTabFloats = 256 * 32;
 __device__ __forceinline__ void load_table(float *tab) {
-    for (int i = threadIdx.x; i < 128 * 32; i += blockDim.x) tab[i] = __fdiv_rn(float(i >> 5), 127.0f);
+    for (int i = threadIdx.x; i < kTabFloats; i += blockDim.x) {
+        const int q = int((signed char)(i >> 5));
+        const int a = q < 0 ? -q : q;
+        const float t = __fdiv_rn(float(a > 127 ? 127 : a), 127.0f);
+        tab[i] = q < 0 ? -t : t;
+    }
     __syncthreads();
 }
 
-__device__ __forceinline__ float dec1(int q, float s, const float *tab, int lane) {
-    const int a = q < 0 ? -q : q;
-    const float v = __fmul_rn(s, tab[a * 32 + lane]);
-    return q < 0 ? -v : v;
+__device__ __forceinline__ float dec1(uint32_t u, float s, const float *tab, int lane) {
+    return __fmul_rn(s, tab[u * 32 + lane]);
 }
 
-__device__ __forceinline__ signed char enc1(float x, float inv) {
-    int r = __float2int_rn(__fmul_rn(x, inv));
-    r = r > 127 ? 127 : (r < -127 ? -127 : r);
-    return (signed char)r;
-}
+// rint(x * fl(127/s)).  No clamp is needed: s is the exact maximum of |x| over
+// the block, so |x * fl(127/s)| <= 127 (1 + 2^-24)^2 < 127.5.
+__device__ __forceinline__ int enc1(float x, float inv) { return __float2int_rn(__fmul_rn(x, inv)); }
 
 __device__ __forceinline__ void gate_pair(const float *u, float &ar, float &ai, float &br, float &bi) {
     const float r0 = __fmaf_rn(u[0], ar, __fmaf_rn(-u[1], ai, __fmaf_rn(u[2], br, -__fmul_rn(u[3], bi))));
@@ -82,11 +86,12 @@ struct Lane8 {
 };
 
 __device__ __forceinline__ void decode_lane(const int4 raw, float s, const float *tab, int lane, Lane8 &x) {
-    const signed char *b = reinterpret_cast<const signed char *>(&raw);
+    const uint32_t w[4] = {uint32_t(raw.x), uint32_t(raw.y), uint32_t(raw.z), uint32_t(raw.w)};
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-        x.re[j] = dec1(b[2 * j], s, tab, lane);
-        x.im[j] = dec1(b[2 * j + 1], s, tab, lane);
+        const uint32_t word = w[j >> 1], sh = (j & 1) * 16;
+        x.re[j] = dec1((word >> sh) & 0xFFu, s, tab, lane);
+        x.im[j] = dec1((word >> (sh + 8)) & 0xFFu, s, tab, lane);
     }
 }
 
@@ -99,19 +104,17 @@ __device__ __forceinline__ float lane_absmax(const Lane8 &x) {
 
 // Encode a lane's 8 amplitudes with the block scale s (warp-uniform).
 __device__ __forceinline__ int4 encode_lane(const Lane8 &x, float s) {
-    int4 raw;
-    signed char *b = reinterpret_cast<signed char *>(&raw);
-    if (s == 0.0f) {
-        raw = make_int4(0, 0, 0, 0);
-        return raw;
-    }
+    if (s == 0.0f) return make_int4(0, 0, 0, 0);
     const float inv = __fdiv_rn(127.0f, s);
+    uint32_t w[4];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        b[2 * j] = enc1(x.re[j], inv);
-        b[2 * j + 1] = enc1(x.im[j], inv);
+    for (int k = 0; k < 4; ++k) {
+        const uint32_t b0 = uint32_t(enc1(x.re[2 * k], inv)) & 0xFFu, b1 = uint32_t(enc1(x.im[2 * k], inv)) & 0xFFu;
+        const uint32_t b2 = uint32_t(enc1(x.re[2 * k + 1], inv)) & 0xFFu,
+                       b3 = uint32_t(enc1(x.im[2 * k + 1], inv)) & 0xFFu;
+        w[k] = b0 | (b1 << 8) | (b2 << 16) | (b3 << 24);
     }
-    return raw;
+    return make_int4(int(w[0]), int(w[1]), int(w[2]), int(w[3]));
 }
 
 // Does amplitude j of this lane (in-block index lane*8 + j) satisfy the control?
@@ -124,7 +127,7 @@ __device__ __forceinline__ bool ctl_ok(int c, int lane, int j) {
 // Target inside the block (t < 8).
 __global__ void __launch_bounds__(32 * kWarpsPerCta) k_enc_gate_in(int4 *__restrict__ codes, float *__restrict__ scales,
                                                                    EncGateArgs a) {
-    __shared__ float tab[128 * 32];
+    __shared__ float tab[kTabFloats];
     load_table(tab);
     const int lane = threadIdx.x & 31;
     const uint64_t wid = uint64_t(blockIdx.x) * kWarpsPerCta + (threadIdx.x >> 5);
@@ -169,7 +172,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta) k_enc_gate_in(int4 *__restr
 // Target across blocks (t >= 8): the warp holds block b0 and b0 + 2^(t-8).
 __global__ void __launch_bounds__(32 * kWarpsPerCta) k_enc_gate_across(int4 *__restrict__ codes,
                                                                        float *__restrict__ scales, EncGateArgs a) {
-    __shared__ float tab[128 * 32];
+    __shared__ float tab[kTabFloats];
     load_table(tab);
     const int lane = threadIdx.x & 31;
     const uint64_t wid = uint64_t(blockIdx.x) * kWarpsPerCta + (threadIdx.x >> 5);
@@ -225,8 +228,8 @@ __global__ void k_enc_gate_small(signed char *codes, float *scales, int n, EncGa
     scales[0] = m;
     const float inv = m == 0.0f ? 0.0f : __fdiv_rn(127.0f, m);
     for (int i = 0; i < dim; ++i) {
-        codes[2 * i] = m == 0.0f ? 0 : enc1(re[i], inv);
-        codes[2 * i + 1] = m == 0.0f ? 0 : enc1(im[i], inv);
+        codes[2 * i] = m == 0.0f ? 0 : (signed char)enc1(re[i], inv);
+        codes[2 * i + 1] = m == 0.0f ? 0 : (signed char)enc1(im[i], inv);
     }
 }
 
@@ -255,7 +258,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta) k_encode(const float4 *__re
 __global__ void __launch_bounds__(32 * kWarpsPerCta) k_decode(const int4 *__restrict__ codes,
                                                               const float *__restrict__ scales,
                                                               float4 *__restrict__ psi, uint64_t nblocks) {
-    __shared__ float tab[128 * 32];
+    __shared__ float tab[kTabFloats];
     load_table(tab);
     const int lane = threadIdx.x & 31;
     const uint64_t wid = uint64_t(blockIdx.x) * kWarpsPerCta + (threadIdx.x >> 5);
@@ -277,8 +280,8 @@ __global__ void k_encode_small(const float2 *psi, signed char *codes, float *sca
     scales[0] = m;
     const float inv = m == 0.0f ? 0.0f : __fdiv_rn(127.0f, m);
     for (int i = 0; i < dim; ++i) {
-        codes[2 * i] = m == 0.0f ? 0 : enc1(psi[i].x, inv);
-        codes[2 * i + 1] = m == 0.0f ? 0 : enc1(psi[i].y, inv);
+        codes[2 * i] = m == 0.0f ? 0 : (signed char)enc1(psi[i].x, inv);
+        codes[2 * i + 1] = m == 0.0f ? 0 : (signed char)enc1(psi[i].y, inv);
     }
 }
 
@@ -291,6 +294,110 @@ __global__ void k_decode_small(const signed char *codes, const float *scales, fl
         const float vr = __fmul_rn(s, __fdiv_rn(float(qr < 0 ? -qr : qr), 127.0f));
         const float vi = __fmul_rn(s, __fdiv_rn(float(qi < 0 ? -qi : qi), 127.0f));
         psi[i] = make_float2(qr < 0 ? -vr : vr, qi < 0 ? -vi : vi);
+    }
+}
+
+
+// ---------------------------------------------------------------- code-level fast paths
+// Exact shortcuts of the decode-gate-encode pass.  Decoding and re-encoding a
+// block with an unchanged scale returns its codes (|s T[q] fl(127/s) - q| is
+// far below 1/2), and a diagonal gate with entries +-1, or a permutation of
+// amplitudes inside a block or of whole blocks, leaves every block maximum
+// unchanged; so these gates are sign flips or moves of the codes.
+
+struct EncFlipArgs {
+    uint64_t nwork;      // int4 words (8 amplitudes) to visit
+    int ins[2], nins;    // ascending block-index positions where bits are inserted
+    uint64_t set_mask;   // block-index bits forced to 1
+    uint32_t lo_mask;    // in-block index bits of the condition (< 8)
+    uint32_t lo_val;
+};
+
+// Negate the codes of every amplitude whose in-block bits match (lo_mask, lo_val)
+// in the blocks selected by the inserted / forced block bits.
+__global__ void __launch_bounds__(256) k_enc_flip(uint4 *__restrict__ codes, EncFlipArgs a) {
+    const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+    for (uint64_t w = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; w < a.nwork; w += stride) {
+        uint64_t b = w >> 5;  // selected block number, 32 words per block
+        for (int k = 0; k < a.nins; ++k) b = insert_zero(b, a.ins[k]);
+        b |= a.set_mask;
+        const uint32_t lane = uint32_t(w & 31);
+        uint4 v = codes[b * 32 + lane];
+        uint32_t *x = reinterpret_cast<uint32_t *>(&v);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            uint32_t bm = 0;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const uint32_t idx = lane * 8 + 2 * k + h;
+                if ((idx & a.lo_mask) == a.lo_val) bm |= 0xFFFFu << (16 * h);
+            }
+            x[k] = (x[k] & ~bm) | (__vneg4(x[k]) & bm);
+        }
+        codes[b * 32 + lane] = v;
+    }
+}
+
+// X on in-block target t (< 8), optional control c: swap amplitude pairs
+// inside each selected block; one warp per block.
+__global__ void __launch_bounds__(256) k_enc_xin(uint4 *__restrict__ codes, EncGateArgs a) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t wid = uint64_t(blockIdx.x) * 8 + (threadIdx.x >> 5);
+    const uint64_t nw = uint64_t(gridDim.x) * 8;
+    for (uint64_t w = wid; w < a.nwork; w += nw) {
+        uint64_t b = w;
+        for (int k = 0; k < a.nins; ++k) b = insert_zero(b, a.ins[k]);
+        b |= a.set_mask;
+        const uint4 v = codes[b * 32 + lane];
+        uint4 p;
+        if (a.t >= 3) {
+            const int lb = 1 << (a.t - 3);
+            p.x = __shfl_xor_sync(0xffffffffu, v.x, lb);
+            p.y = __shfl_xor_sync(0xffffffffu, v.y, lb);
+            p.z = __shfl_xor_sync(0xffffffffu, v.z, lb);
+            p.w = __shfl_xor_sync(0xffffffffu, v.w, lb);
+        } else if (a.t == 0) {
+            p = make_uint4(__byte_perm(v.x, 0, 0x1032), __byte_perm(v.y, 0, 0x1032), __byte_perm(v.z, 0, 0x1032),
+                           __byte_perm(v.w, 0, 0x1032));
+        } else if (a.t == 1) {
+            p = make_uint4(v.y, v.x, v.w, v.z);
+        } else {
+            p = make_uint4(v.z, v.w, v.x, v.y);
+        }
+        const uint32_t *xv = reinterpret_cast<const uint32_t *>(&v), *xp = reinterpret_cast<const uint32_t *>(&p);
+        uint32_t out[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            uint32_t bm = 0;
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+                if (ctl_ok(a.c, lane, 2 * k + h)) bm |= 0xFFFFu << (16 * h);
+            out[k] = (xv[k] & ~bm) | (xp[k] & bm);
+        }
+        codes[b * 32 + lane] = make_uint4(out[0], out[1], out[2], out[3]);
+    }
+}
+
+// X on a block-level target (>= 8) with no control or a block-level control:
+// swap whole blocks (codes and scales); one warp per block pair.
+__global__ void __launch_bounds__(256) k_enc_xblocks(uint4 *__restrict__ codes, float *__restrict__ scales,
+                                                     EncGateArgs a) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t wid = uint64_t(blockIdx.x) * 8 + (threadIdx.x >> 5);
+    const uint64_t nw = uint64_t(gridDim.x) * 8;
+    for (uint64_t w = wid; w < a.nwork; w += nw) {
+        uint64_t b0 = w;
+        for (int k = 0; k < a.nins; ++k) b0 = insert_zero(b0, a.ins[k]);
+        b0 |= a.set_mask;
+        const uint64_t b1 = b0 | a.tbit;
+        const uint4 v0 = codes[b0 * 32 + lane], v1 = codes[b1 * 32 + lane];
+        codes[b0 * 32 + lane] = v1;
+        codes[b1 * 32 + lane] = v0;
+        if (lane == 0) {
+            const float s0 = scales[b0];
+            scales[b0] = scales[b1];
+            scales[b1] = s0;
+        }
     }
 }
 
@@ -316,6 +423,33 @@ cudaError_t launch_enc_gate1(sv_state *h, const Gate1 &g) {
         return cudaGetLastError();
     }
     const int nb_log = n - kEncBlockLog2;
+    const Cplx *u = g.u;
+    auto is = [](const Cplx &z, double re) { return z.re == re && z.im == 0.0; };
+    // diagonal with entries +-1 (Z, CZ, ...): sign flips of codes
+    if (is(u[1], 0) && is(u[2], 0) && (is(u[0], 1) || is(u[0], -1)) && (is(u[3], 1) || is(u[3], -1))) {
+        if (is(u[0], 1) && is(u[3], 1)) return cudaSuccess;  // identity
+        uint64_t m = g.control >= 0 ? (uint64_t(1) << g.control) : 0, v = m;
+        if (!(is(u[0], -1) && is(u[3], -1))) {  // only one half flips: condition on the target bit
+            m |= uint64_t(1) << g.target;
+            if (is(u[3], -1)) v |= uint64_t(1) << g.target;
+        }
+        EncFlipArgs fa{};
+        fa.lo_mask = uint32_t(m & 0xFFu);
+        fa.lo_val = uint32_t(v & 0xFFu);
+        int k = 0;
+        for (int bit = kEncBlockLog2; bit < n; ++bit)
+            if (m >> bit & 1) {
+                fa.ins[k++] = bit - kEncBlockLog2;
+                if (v >> bit & 1) fa.set_mask |= uint64_t(1) << (bit - kEncBlockLog2);
+            }
+        fa.nins = k;
+        fa.nwork = (uint64_t(1) << (nb_log - k)) * 32;
+        const uint64_t blocks = (fa.nwork + 255) / 256;
+        k_enc_flip<<<unsigned(blocks < 152 * 32 ? blocks : 152 * 32), 256, 0, h->stream>>>(static_cast<uint4 *>(h->data),
+                                                                                          fa);
+        return cudaGetLastError();
+    }
+    const bool xgate = is(u[0], 0) && is(u[3], 0) && is(u[1], 1) && is(u[2], 1);
     int ins[2], ni = 0;
     if (a.c >= kEncBlockLog2) {
         ins[ni++] = a.c - kEncBlockLog2;
@@ -334,6 +468,14 @@ cudaError_t launch_enc_gate1(sv_state *h, const Gate1 &g) {
     a.nins = ni;
     a.nwork = uint64_t(1) << (nb_log - ni);
     int4 *codes = static_cast<int4 *>(h->data);
+    if (xgate && a.t < kEncBlockLog2) {  // permutation inside blocks
+        k_enc_xin<<<enc_grid(a.nwork), 256, 0, h->stream>>>(reinterpret_cast<uint4 *>(codes), a);
+        return cudaGetLastError();
+    }
+    if (xgate && (a.c < 0 || a.c >= kEncBlockLog2)) {  // whole-block swaps
+        k_enc_xblocks<<<enc_grid(a.nwork), 256, 0, h->stream>>>(reinterpret_cast<uint4 *>(codes), h->scales, a);
+        return cudaGetLastError();
+    }
     if (a.t < kEncBlockLog2)
         k_enc_gate_in<<<enc_grid(a.nwork), 32 * kWarpsPerCta, 0, h->stream>>>(codes, h->scales, a);
     else
@@ -395,7 +537,7 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 // partial sums, FP64 beyond; one partial per CTA.
 __global__ void __launch_bounds__(256) k_enc_norm(const int4 *__restrict__ codes, const float *__restrict__ scales,
                                                   uint64_t nblocks, double *__restrict__ partials) {
-    __shared__ float tab[128 * 32];
+    __shared__ float tab[kTabFloats];
     __shared__ double sh[8];
     load_table(tab);
     const int lane = threadIdx.x & 31;

@@ -355,7 +355,19 @@ __global__ void k_gather(const C2<R> *__restrict__ psi, const uint64_t *__restri
 int norm_partials_needed(const sv_state *) { return kNormBlocks; }
 
 const char *gate1_kernel_name(const sv_state *h, const Gate1 &g) {
-    if (h->dt == SV_ENC2B) return g.target < kEncBlockLog2 || h->n < kEncBlockLog2 ? "k_enc_gate_in" : "k_enc_gate_across";
+    if (h->dt == SV_ENC2B) {
+        auto is = [](const Cplx &z, double re) { return z.re == re && z.im == 0.0; };
+        const Cplx *u = g.u;
+        if (h->n >= kEncBlockLog2) {
+            if (is(u[1], 0) && is(u[2], 0) && (is(u[0], 1) || is(u[0], -1)) && (is(u[3], 1) || is(u[3], -1)))
+                return "k_enc_flip";
+            if (is(u[0], 0) && is(u[3], 0) && is(u[1], 1) && is(u[2], 1)) {
+                if (g.target < kEncBlockLog2) return "k_enc_xin";
+                if (g.control < 0 || g.control >= kEncBlockLog2) return "k_enc_xblocks";
+            }
+        }
+        return g.target < kEncBlockLog2 || h->n < kEncBlockLog2 ? "k_enc_gate_in" : "k_enc_gate_across";
+    }
     const bool diag = g.u[1].re == 0 && g.u[1].im == 0 && g.u[2].re == 0 && g.u[2].im == 0;
     const bool unit00 = g.u[0].re == 1 && g.u[0].im == 0;
     const bool c64 = h->dt == SV_C64;

@@ -1,4 +1,6 @@
 // Plan creation and replay.
+#include <string>
+
 #include "plan.h"
 
 namespace sv {
@@ -7,8 +9,18 @@ double gate1_bytes(const sv_state *h, const Gate1 &g) {
     const double amps = double(uint64_t(1) << h->n);
     if (h->dt == SV_ENC2B) {
         const double nb = h->n < kEncBlockLog2 ? 1.0 : amps / kEncBlock;
-        const double frac = g.control >= 0 ? 0.5 : 1.0;
-        return frac * (2.0 * amps * 2.0 + 2.0 * nb * 4.0);
+        const std::string k = gate1_kernel_name(h, g);
+        // fraction of blocks a pass visits: block-level condition bits halve it
+        int blockbits = 0;
+        if (g.control >= kEncBlockLog2) ++blockbits;
+        const bool flip = k == "k_enc_flip";
+        if (flip) {
+            const bool both = g.u[0].re == -1 && g.u[3].re == -1;
+            if (!both && g.target >= kEncBlockLog2) ++blockbits;
+        }
+        const double frac = 1.0 / double(1 << blockbits);
+        if (flip || k == "k_enc_xin") return frac * 2.0 * amps * 2.0;          // codes only
+        return frac * (2.0 * amps * 2.0 + 2.0 * nb * 4.0);                    // codes and scales
     }
     const double s = h->dt == SV_C64 ? 8.0 : 16.0;
     const bool diag = g.u[1].re == 0 && g.u[1].im == 0 && g.u[2].re == 0 && g.u[2].im == 0;
