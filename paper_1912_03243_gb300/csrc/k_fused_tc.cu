@@ -14,7 +14,7 @@
 //
 // Per CTA (persistent, one per SM, 256 threads) and per tile of 2^13
 // amplitudes (the k block qubits plus the lowest other qubits):
-//   cp.async the tile into shared memory (FP32) -> convert to Bh, Bl in the
+//   cp.async the tile into shared memory (FP32, swizzled) -> convert to Bh, Bl in the
 //   K-major no-swizzle canonical layout -> one thread issues 3 x 8
 //   tcgen05.mma (K = 16 each) into a 128-column TMEM accumulator and commits
 //   to an mbarrier -> all threads wait (bounded by %globaltimer) -> each warp
@@ -48,6 +48,13 @@ __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
+// Staging tile layout: 16-byte chunk c (amplitudes 2c, 2c+1) lives at chunk
+// c ^ ((c>>3 ^ c>>6 ^ c>>9) & 7), which spreads both the B-operand reads
+// (lanes along group bits) and the accumulator writes (lanes along block
+// bits) over the banks.
+__device__ __forceinline__ uint32_t swz(uint32_t c) { return c ^ (((c >> 3) ^ (c >> 6) ^ (c >> 9)) & 7u); }
+__device__ __forceinline__ uint32_t sxpos(uint32_t j) { return (swz(j >> 1) << 1) | (j & 1u); }
+
 __device__ __forceinline__ uint64_t globaltimer() {
     uint64_t t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -77,8 +84,6 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64
         : "memory");
 }
 
-__device__ __forceinline__ uint16_t bf16_bits(__nv_bfloat16 h) { return *reinterpret_cast<uint16_t *>(&h); }
-
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
     uint32_t r[32];
     asm volatile(
@@ -103,9 +108,34 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fused_tc(float2 *__restrict__
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
+    // index tables in shared memory: lanes read different entries (a kernel-
+    // parameter array would serialise on the constant cache)
+    __shared__ uint16_t tL[64], tP[64], tN[128];   // swizzled staging offsets of l, p, n
+    __shared__ uint64_t gHi[16];                    // global offset of chunk bits 8..11
+    __shared__ uint16_t sHi[16];                    // swizzled chunk of chunk bits 8..11
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t mbar_a = smem_u32(&mbar);
 
+    for (int i = tid; i < 128; i += kTcThreads) {
+        tN[i] = uint16_t(sxpos(a.offN[i]));
+        if (i < 64) {
+            tL[i] = uint16_t(sxpos(a.offL[i]));
+            tP[i] = uint16_t(sxpos(a.offP[i]));
+        }
+        if (i < 16) {  // chunk c = tid + 256 i: tile index bits 9..12 of j = 2c
+            const uint32_t j = uint32_t(i) << 9;
+            uint64_t g = 0;
+            for (int q = 0; q < kTcM; ++q)
+                if (j >> q & 1) g |= uint64_t(1) << a.tile_pos[q];
+            gHi[i] = g;
+            sHi[i] = uint16_t(swz(uint32_t(i) << 8));
+        }
+    }
+    // this thread's chunk bits 0..7 (tile index bits 1..8)
+    uint64_t gLo = 0;
+    for (int q = 1; q <= 8; ++q)
+        if ((uint32_t(tid) << 1) >> q & 1) gLo |= uint64_t(1) << a.tile_pos[q];
+    const uint32_t sLo = swz(uint32_t(tid));
     if (tid == 0) {
         abort_flag = 0;
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mbar_a) : "memory");
@@ -125,41 +155,33 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fused_tc(float2 *__restrict__
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     const uint32_t tmem = tmem_slot;
 
-    const uint32_t lmask = (1u << a.lc) - 1u;
     uint32_t phase = 0;
     for (uint64_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
         uint64_t base = 0;
         for (int q = 0; q < a.nouter; ++q) base |= ((tile >> q) & 1ull) << a.outer_pos[q];
-        // load: 16-byte chunks (2 amplitudes), tile index j = 2c
-        for (int c = tid; c < (1 << (kTcM - 1)); c += kTcThreads) {
-            const uint32_t j = uint32_t(c) * 2;
-            uint64_t g = base | (j & lmask);
-            for (int q = a.lc; q < kTcM; ++q) g |= uint64_t((j >> q) & 1u) << a.tile_pos[q];
-            cp_async16(smem_u32(sX + j), psi + g);
-        }
+        // load: 16-byte chunks c = tid + 256 i (2 amplitudes, tile index 2c);
+        // offsets split into a per-thread and a per-i part (disjoint bits)
+#pragma unroll
+        for (int i = 0; i < 16; ++i)
+            cp_async16(smem_u32(sX + 2 * (sLo ^ sHi[i])), psi + (base | gLo | gHi[i]));
         cp_async_wait_all();
         __syncthreads();
         // convert: one task = one B row n and 8 consecutive K elements (16 B of Bh and of Bl)
-        const int twoD = 2 << a.k;
+        const int klog = a.k + 1, rmask = (2 << a.k) - 1;  // 2d = 2^(k+1)
         for (int t = tid; t < 16 * 128; t += kTcThreads) {
             const int nrow = t & 127, q8 = t >> 7;
+            const uint32_t sn = tN[nrow];
             uint32_t hw[4], lw[4];
 #pragma unroll
-            for (int e = 0; e < 8; e += 2) {
-                uint16_t hb[2], lb[2];
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int kk = q8 * 8 + e + h;
-                    const int p = kk / twoD, r = kk % twoD;
-                    const float2 amp = sX[a.offL[r >> 1] | a.offP[p] | a.offN[nrow]];
-                    const float x = (r & 1) ? amp.y : amp.x;
-                    const __nv_bfloat16 hi = __float2bfloat16_rn(x);
-                    const __nv_bfloat16 lo = __float2bfloat16_rn(x - __bfloat162float(hi));
-                    hb[h] = bf16_bits(hi);
-                    lb[h] = bf16_bits(lo);
-                }
-                hw[e >> 1] = uint32_t(hb[0]) | (uint32_t(hb[1]) << 16);
-                lw[e >> 1] = uint32_t(lb[0]) | (uint32_t(lb[1]) << 16);
+            for (int e = 0; e < 8; e += 2) {  // elements kk, kk+1: re and im of one amplitude
+                const int kk = q8 * 8 + e;
+                const int p = kk >> klog, r = kk & rmask;
+                const float2 amp = sX[sn ^ tL[r >> 1] ^ tP[p]];
+                const __nv_bfloat162 hi = __float22bfloat162_rn(amp);
+                const float2 hf = __bfloat1622float2(hi);
+                const __nv_bfloat162 lo = __float22bfloat162_rn(make_float2(amp.x - hf.x, amp.y - hf.y));
+                hw[e >> 1] = *reinterpret_cast<const uint32_t *>(&hi);
+                lw[e >> 1] = *reinterpret_cast<const uint32_t *>(&lo);
             }
             const uint32_t off = uint32_t((nrow & 7) * 16 + q8 * 128 + (nrow >> 3) * 2048);
             *reinterpret_cast<uint4 *>(sBh + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
@@ -207,8 +229,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fused_tc(float2 *__restrict__
         // read D: warp w reads lanes 32 (w % 4) .. +31, columns 64 (w / 4) .. +63
         {
             const int row = 32 * (warp & 3) + lane;
-            const int p = row / twoD, r = row % twoD;
-            const uint32_t jrow = a.offL[r >> 1] | a.offP[p];
+            const int p = row >> klog, r = row & rmask;
+            const uint32_t srow = tL[r >> 1] ^ tP[p];
             float *sXf = reinterpret_cast<float *>(sX);
 #pragma unroll
             for (int half = 0; half < 2; ++half) {
@@ -216,18 +238,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fused_tc(float2 *__restrict__
                 float v[32];
                 tmem_ld32(tmem + (uint32_t(32 * (warp & 3)) << 16) + uint32_t(c0), v);
 #pragma unroll
-                for (int i = 0; i < 32; ++i) sXf[2 * (jrow | a.offN[c0 + i]) + (r & 1)] = v[i];
+                for (int i = 0; i < 32; ++i) sXf[2 * (srow ^ tN[c0 + i]) + (r & 1)] = v[i];
             }
         }
         asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
         __syncthreads();
         // store
-        for (int c = tid; c < (1 << (kTcM - 1)); c += kTcThreads) {
-            const uint32_t j = uint32_t(c) * 2;
-            uint64_t g = base | (j & lmask);
-            for (int q = a.lc; q < kTcM; ++q) g |= uint64_t((j >> q) & 1u) << a.tile_pos[q];
-            *reinterpret_cast<float4 *>(psi + g) = *reinterpret_cast<const float4 *>(sX + j);
-        }
+#pragma unroll
+        for (int i = 0; i < 16; ++i)
+            *reinterpret_cast<float4 *>(psi + (base | gLo | gHi[i])) =
+                *reinterpret_cast<const float4 *>(sX + 2 * (sLo ^ sHi[i]));
         __syncthreads();
     }
     if (abort_flag && tid == 0) atomicExch(err, int(SV_ERR_TIMEOUT));
