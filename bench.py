@@ -289,7 +289,7 @@ def time_plan(S, state, plan, steps, warmup, world, with_events=True):
     return max_over_ranks(world, t), per_launch
 
 
-def dominant_roofline(info, per_launch, steps, peak, peak_kind):
+def dominant_roofline(info, per_launch, steps, peak, peak_kind, n=None):
     tot, cnt, byt = {}, {}, {}
     for k in range(steps):
         for i, (name, b) in enumerate(info):
@@ -298,7 +298,9 @@ def dominant_roofline(info, per_launch, steps, peak, peak_kind):
             byt[name] = byt.get(name, 0.0) + b
     dom = max(tot, key=tot.get)
     achieved = byt[dom] / (tot[dom] / 1e3) / 1e9
+    traffic, tsrc = traffic_from_profiles(dom.split("<")[0], n) if n is not None else (None, None)
     return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": traffic, "traffic_source": os.path.basename(tsrc) if tsrc else None,
             "kernel": dom, "launches": cnt[dom], "avg_launch_ms": tot[dom] / cnt[dom],
             "bytes_per_launch": byt[dom] / cnt[dom], "peak_kind": peak_kind,
             "share_of_step": tot[dom] / sum(tot.values())}
@@ -325,7 +327,7 @@ def bench_enc2b(S, C, args, world, peak, peak_kind):
                        f"two-byte code ({need / 2**30:.1f} GiB)",
            "gates_per_s": plan.gates * 2 / t, "ms_per_gate": 1e3 * t / (2 * plan.gates),
            "gbs": plan.bytes * 2 / t / 1e9, "full_circuit_s_est": len(circ) * t / (2 * plan.gates),
-           "roofline": dominant_roofline(info, per_launch, 2, peak, peak_kind)}
+           "roofline": dominant_roofline(info, per_launch, 2, peak, peak_kind, n)}
     plan.free()
     st.free()
     del st
@@ -431,13 +433,15 @@ def run_ours(args, world, rank, local):
         if other == mode or args.compare_steps <= 0:
             continue
         pg = state.plan(circ, other)
-        tp, _ = time_plan(S, state, pg, args.compare_steps, 1, world, with_events=False)
-        kernels = sorted({k for k, _ in pg.launch_info()})
+        pinfo = pg.launch_info()
+        tp, plaunch = time_plan(S, state, pg, args.compare_steps, 1, world)
+        kernels = sorted({k for k, _ in pinfo})
         compare[other] = {"gates_per_s": pg.gates * args.compare_steps * world / tp,
                           "gbs": pg.bytes * args.compare_steps * world / tp / 1e9, "launches_per_step": pg.passes,
                           "ms_per_step": 1e3 * tp / args.compare_steps,
                           "layers_per_s": args.depth * args.compare_steps * world / tp,
-                          "kernels": kernels[:4]}
+                          "kernels": kernels[:4],
+                          "roofline": dominant_roofline(pinfo, plaunch, args.compare_steps, hbm_peak, peak_kind, args.n)}
         if other == "fused":
             state.set_basis(0)
             pg.execute()

@@ -69,9 +69,11 @@ typedef enum {
 /* Circuit execution modes (sv_run_circuit, sv_plan_create). */
 typedef enum {
     SV_MODE_PERGATE = 0,     /* one HBM pass per gate (Eq. 1 per gate) */
-    SV_MODE_TILED = 1,       /* several gates per HBM pass in shared memory */
-    SV_MODE_FUSED = 2        /* tiled passes whose gates are fused into k-qubit
-                                blocks applied on the tensor cores */
+    SV_MODE_TILED = 1,       /* many gates per HBM pass: 2^13-amplitude tiles in
+                                shared memory, one compiled kernel per pass */
+    SV_MODE_FUSED = 2        /* gates fused into dense k-qubit blocks (k = 3..6
+                                chosen by the planner), one HBM pass per block on
+                                the tensor cores */
 } sv_mode;
 
 /* ---- lifecycle --------------------------------------------------------- */
@@ -124,9 +126,12 @@ sv_status sv_apply_gate(sv_handle h, int target, int control, const double *U);
 
 /* Sec. 2: a k-qubit gate as a dense 2^k x 2^k matrix on the listed qubits
  * (local index bit j <-> qubits[j]; qubits[0] is the least significant).
- * 1 <= k <= 6, qubits distinct.  SV_C64 applies it on the tensor cores with
- * split-precision BF16 products and FP32 accumulation; SV_C128 in FP64 on
- * the CUDA cores.  Errors: SV_ERR_ARG, SV_ERR_DTYPE (SV_ENC2B). */
+ * 1 <= k <= 6, qubits distinct.  SV_C64 states of n >= 13 apply it on the
+ * tensor cores (tcgen05) with split-precision BF16 products (A_hi B_hi +
+ * A_hi B_lo + A_lo B_hi) and FP32 accumulation; smaller SV_C64 states in
+ * FP32 and SV_C128 in FP64 on the CUDA cores.  The tensor-core kernel's only
+ * wait is bounded; if it gives up, the next synchronising call returns
+ * SV_ERR_TIMEOUT.  Errors: SV_ERR_ARG, SV_ERR_DTYPE (SV_ENC2B). */
 sv_status sv_apply_fused(sv_handle h, int k, const int *qubits, const double *U);
 
 /* ---- circuits -------------------------------------------------------------- */
