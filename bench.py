@@ -41,7 +41,8 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="auto", choices=["auto", "pergate", "tiled", "fused"])
-    ap.add_argument("--n", type=int, default=32)
+    ap.add_argument("--qubits", "--n", dest="n", type=int, default=32,
+                    help="state size; --qubits under torch.distributed.run, whose own parser takes --n as an abbreviation")
     ap.add_argument("--depth", type=int, default=24)
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--compare-steps", type=int, default=1,
@@ -147,7 +148,8 @@ def max_over_ranks(world, value: float) -> float:
     import torch
     import torch.distributed as dist
 
-    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    device = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 

@@ -230,6 +230,17 @@ sv_status sv_amplitudes_noalloc(const void *state, int n, sv_dtype dt, size_t m,
 sv_status sv_cut_amplitudes(const char *text, int n, uint64_t maskA, int form, size_t m,
                             const uint64_t *z, double *out, int *n_cut_out, void *stream);
 
+/* The part of the Eq. 3 sum over the branches s with s mod 2^nparts_log2 ==
+ * part (Sec. 4: the terms are independent, so parts can be computed on
+ * different GPUs or processes and added).  The low nparts_log2 branch bits
+ * are fixed, which turns their branch operators into plain diagonal gates and
+ * halves the batched vectors per fixed bit.  Summing all 2^nparts_log2 parts
+ * gives sv_cut_amplitudes.  0 <= nparts_log2 <= 16, part < 2^nparts_log2
+ * (parts with no branch give zeros).  Other arguments and errors as
+ * sv_cut_amplitudes. */
+sv_status sv_cut_amplitudes_part(const char *text, int n, uint64_t maskA, int form, uint64_t part, int nparts_log2,
+                                 size_t m, const uint64_t *z, double *out, int *n_cut_out, void *stream);
+
 /* ---- host-only helpers (no GPU needed) -------------------------------------------- */
 
 /* The library's own matrix for a named gate of the circuit format: writes 8

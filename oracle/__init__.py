@@ -67,6 +67,8 @@ def lib() -> ctypes.CDLL:
             L.orc_eq2_terms.restype = None
             L.orc_cut_amplitudes.argtypes = [ctypes.c_char_p, ctypes.c_int, ctypes.c_uint64, ctypes.c_int,
                                              ctypes.c_int64, u64p, dp, ip]
+            L.orc_cut_amplitudes_part.argtypes = [ctypes.c_char_p, ctypes.c_int, ctypes.c_uint64, ctypes.c_int,
+                                                  ctypes.c_uint64, ctypes.c_int, ctypes.c_int64, u64p, dp, ip]
             _lib = L
     return _lib
 
@@ -231,6 +233,20 @@ def eq2_terms():
     dm = np.zeros(4)
     lib().orc_eq2_terms(_dp(x), _dp(dp_), _dp(dm))
     return complex(x[0], x[1]), dp_.view(np.complex128).copy(), dm.view(np.complex128).copy()
+
+
+def cut_amplitudes_part(circuit, mask_a: int, z, part: int, nparts_log2: int, form: int = 0,
+                        n: int | None = None):
+    """Partial Eq. 3 sum over the terms s with s mod 2^nparts_log2 == part."""
+    if n is None:
+        n = circuit.n
+    zz = np.ascontiguousarray(z, dtype=np.uint64)
+    out = np.zeros(2 * zz.size, dtype=np.float64)
+    s = ctypes.c_int(0)
+    _check(lib().orc_cut_amplitudes_part(_text(circuit), n, ctypes.c_uint64(mask_a), form, ctypes.c_uint64(part),
+                                         nparts_log2, zz.size, zz.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                                         _dp(out), ctypes.byref(s)))
+    return out.view(np.complex128).copy(), s.value
 
 
 def cut_amplitudes(circuit, mask_a: int, z, form: int = 0, n: int | None = None):

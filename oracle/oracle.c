@@ -546,8 +546,24 @@ static void apply_diag1(cplx *psi, int n, int q, const cplx d[2]) {
  * complex numbers.  form 0: projector decomposition (weight 1); form 1:
  * Eq. 2 (weight 1/2 per decomposed gate, CZ only).  n_cut_out, if not NULL,
  * receives S. */
+static int cut_amplitudes_range(const char *text, int n, uint64_t maskA, int form, uint64_t s_lo, uint64_t s_step,
+                                int64_t m, const uint64_t *z, double *out, int *n_cut_out);
+
 int orc_cut_amplitudes(const char *text, int n, uint64_t maskA, int form,
                        int64_t m, const uint64_t *z, double *out, int *n_cut_out) {
+    return cut_amplitudes_range(text, n, maskA, form, 0, 1, m, z, out, n_cut_out);
+}
+
+/* The part of the Eq. 3 sum over the terms s = part, part + 2^p, part + 2 * 2^p,
+ * ... (the terms are independent, Sec. 4, so parts can be summed anywhere). */
+int orc_cut_amplitudes_part(const char *text, int n, uint64_t maskA, int form, uint64_t part, int nparts_log2,
+                            int64_t m, const uint64_t *z, double *out, int *n_cut_out) {
+    if (nparts_log2 < 0 || nparts_log2 > 20 || (part >> nparts_log2)) return ORC_ERR_ARG;
+    return cut_amplitudes_range(text, n, maskA, form, part, (uint64_t)1 << nparts_log2, m, z, out, n_cut_out);
+}
+
+static int cut_amplitudes_range(const char *text, int n, uint64_t maskA, int form, uint64_t s_lo, uint64_t s_step,
+                                int64_t m, const uint64_t *z, double *out, int *n_cut_out) {
     if (form != 0 && form != 1) return ORC_ERR_ARG;
     orc_circuit c;
     int rc = parse_circuit(text, n, &c);
@@ -618,7 +634,7 @@ int orc_cut_amplitudes(const char *text, int n, uint64_t maskA, int form,
         zh[0][j] = za; zh[1][j] = zb;
     }
     double w = form == 1 ? ldexp(1.0, -S) : 1.0;
-    for (uint64_t s = 0; s < ((uint64_t)1 << S); s++) {
+    for (uint64_t s = s_lo; s < ((uint64_t)1 << S); s += s_step) {
         for (int p = 0; p < 2; p++) {
             uint64_t dim = (uint64_t)1 << nh[p];
             memset(psi[p], 0, dim * sizeof(cplx));

@@ -127,8 +127,12 @@ sv_status run_half(Half &h, cudaStream_t st, int S, std::vector<void *> *fns, Ti
 
 using namespace sv;
 
-extern "C" sv_status sv_cut_amplitudes(const char *text, int n, uint64_t maskA, int form, size_t m, const uint64_t *z,
-                                       double *out, int *n_cut_out, void *stream) {
+// Sum over the branches s with s mod 2^plog == part (plog = 0: all of them).
+// The low plog branch bits are then fixed: their branch operators are plain
+// diagonal gates on the halves' qubits, and only the other S - plog bits are
+// batched.
+static sv_status cut_impl(const char *text, int n, uint64_t maskA, int form, uint64_t part, int plog, size_t m,
+                          const uint64_t *z, double *out, int *n_cut_out, void *stream) {
     if (n < 2 || n > 64 || (form != 0 && form != 1) || (m > 0 && (!z || !out))) {
         set_error("bad arguments (n=%d, form=%d)", n, form);
         return SV_ERR_ARG;
@@ -171,10 +175,16 @@ extern "C" sv_status sv_cut_amplitudes(const char *text, int n, uint64_t maskA, 
         set_error("%d decomposed gates (at most 16)", S);
         return SV_ERR_UNSUPPORTED;
     }
+    const int Svar = S > plog ? S - plog : 0;  // batched branch bits
+    if (n_cut_out) *n_cut_out = S;
+    if (S < 64 && (part >> S) != 0) {  // no branch has these low bits
+        for (size_t j = 0; j < 2 * m; ++j) out[j] = 0.0;
+        return SV_OK;
+    }
     for (int p = 0; p < 2; ++p) {
-        half[p].nq = half[p].nlocal + S < kTileM64 ? kTileM64 : half[p].nlocal + S;
+        half[p].nq = half[p].nlocal + Svar < kTileM64 ? kTileM64 : half[p].nlocal + Svar;
         if (half[p].nq > kMaxQubits) {
-            set_error("half %d needs %d qubits (local %d + %d branch bits)", p, half[p].nq, half[p].nlocal, S);
+            set_error("half %d needs %d qubits (local %d + %d branch bits)", p, half[p].nq, half[p].nlocal, Svar);
             return SV_ERR_UNSUPPORTED;
         }
     }
@@ -198,13 +208,22 @@ extern "C" sv_status sv_cut_amplitudes(const char *text, int n, uint64_t maskA, 
         }
         const int qa = side[a] == 0 ? a : b, qb = side[a] == 0 ? b : a;
         const uint64_t la = uint64_t(1) << loc[qa], lb = uint64_t(1) << loc[qb];
-        const uint64_t ka = uint64_t(1) << (half[0].nlocal + k), kb = uint64_t(1) << (half[1].nlocal + k);
+        const bool fixed = k < plog;
+        const int sfix = int((part >> k) & 1);
+        const uint64_t ka = fixed ? 0 : uint64_t(1) << (half[0].nlocal + k - plog);
+        const uint64_t kb = fixed ? 0 : uint64_t(1) << (half[1].nlocal + k - plog);
         if (form == 0) {
-            half[0].gates.push_back(phase_gate(la | ka, la, 0.0));  // bit a = 1, s_k = 0: P0 removes it
-            half[0].gates.push_back(phase_gate(la | ka, ka, 0.0));  // bit a = 0, s_k = 1: P1 removes it
-            half[1].gates.push_back(phase_gate(lb | kb, lb | kb, std::polar(1.0, theta)));
+            if (fixed) {
+                half[0].gates.push_back(phase_gate(la, sfix ? 0 : la, 0.0));  // keep bit a == s_k
+                if (sfix) half[1].gates.push_back(phase_gate(lb, lb, std::polar(1.0, theta)));
+            } else {
+                half[0].gates.push_back(phase_gate(la | ka, la, 0.0));  // bit a = 1, s_k = 0: P0 removes it
+                half[0].gates.push_back(phase_gate(la | ka, ka, 0.0));  // bit a = 0, s_k = 1: P1 removes it
+                half[1].gates.push_back(phase_gate(lb | kb, lb | kb, std::polar(1.0, theta)));
+            }
         } else {
             for (int sb = 0; sb < 2; ++sb) {
+                if (fixed && sb != sfix) continue;
                 cd d[2];
                 eq2_diag(sb, d);
                 const uint64_t sva = sb ? ka : 0, svb = sb ? kb : 0;
@@ -217,7 +236,6 @@ extern "C" sv_status sv_cut_amplitudes(const char *text, int n, uint64_t maskA, 
         if (ins.name == "CX") append_lowered(h, &half[side[b]].gates);
         ++k;
     }
-    if (n_cut_out) *n_cut_out = S;
     if (m == 0) return SV_OK;
 
     // device memory: two batched vectors + bit strings + results
@@ -265,7 +283,7 @@ extern "C" sv_status sv_cut_amplitudes(const char *text, int n, uint64_t maskA, 
     for (int p = 0; p < 2 && s == SV_OK; ++p) {
         std::vector<void *> fns;
         TilePlan<float> tp;
-        s = run_half(half[p], st, S, &fns, &tp);
+        s = run_half(half[p], st, Svar, &fns, &tp);
     }
     if (s == SV_OK) {
         e = cudaMemcpyAsync(dz, zs.data(), bytesZ, cudaMemcpyHostToDevice, st);
@@ -274,7 +292,7 @@ extern "C" sv_status sv_cut_amplitudes(const char *text, int n, uint64_t maskA, 
     if (s == SV_OK) {
         const double w = form == 1 ? std::ldexp(1.0, -S) : 1.0;
         const size_t blocks = (m + 7) / 8 < 4096 ? (m + 7) / 8 : 4096;
-        k_branch_sum<<<unsigned(blocks), 256, 0, st>>>(half[0].d, half[1].d, half[0].nlocal, half[1].nlocal, S, dz,
+        k_branch_sum<<<unsigned(blocks), 256, 0, st>>>(half[0].d, half[1].d, half[0].nlocal, half[1].nlocal, Svar, dz,
                                                        dz + m, m, w, dout);
         s = check_launch(cudaGetLastError(), "k_branch_sum");
     }
@@ -285,4 +303,19 @@ extern "C" sv_status sv_cut_amplitudes(const char *text, int n, uint64_t maskA, 
     if (s == SV_OK) s = sync_stream(st, "sv_cut_amplitudes");
     release();
     return s;
+}
+
+extern "C" sv_status sv_cut_amplitudes(const char *text, int n, uint64_t maskA, int form, size_t m, const uint64_t *z,
+                                       double *out, int *n_cut_out, void *stream) {
+    return cut_impl(text, n, maskA, form, 0, 0, m, z, out, n_cut_out, stream);
+}
+
+extern "C" sv_status sv_cut_amplitudes_part(const char *text, int n, uint64_t maskA, int form, uint64_t part,
+                                            int nparts_log2, size_t m, const uint64_t *z, double *out, int *n_cut_out,
+                                            void *stream) {
+    if (nparts_log2 < 0 || nparts_log2 > 16 || (part >> nparts_log2) != 0) {
+        set_error("bad part %llu of 2^%d", (unsigned long long)part, nparts_log2);
+        return SV_ERR_ARG;
+    }
+    return cut_impl(text, n, maskA, form, part, nparts_log2, m, z, out, n_cut_out, stream);
 }

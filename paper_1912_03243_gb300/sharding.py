@@ -1,0 +1,53 @@
+"""Branch sharding of the decomposition path across processes (Sec. 4: every
+term of the Eq. 3 sum is independent; the paper distributes them over MPI
+ranks).
+
+The 2^S branches are split into 2^p parts by their low p bits
+(p = ceil(log2(world))); rank r sums parts r, r + world, ... and one FP64
+all-reduce of the m complex amplitudes combines them.  That all-reduce is
+the only collective of the path.
+"""
+
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+
+def parts_for_rank(rank: int, world: int) -> tuple[int, list[int]]:
+    """(nparts_log2, the parts this rank sums)."""
+    if world < 1 or not 0 <= rank < world:
+        raise ValueError(f"bad rank {rank} of {world}")
+    p = max(0, math.ceil(math.log2(world)))
+    return p, [part for part in range(1 << p) if part % world == rank]
+
+
+def sharded_sum(partial_fn, m: int, group=None) -> np.ndarray:
+    """Sum partial_fn(part, nparts_log2) -> complex128[m] over this rank's
+    parts, then all-reduce (FP64) across the process group; every rank
+    returns the full sum."""
+    import torch
+    import torch.distributed as dist
+
+    world = dist.get_world_size(group)
+    rank = dist.get_rank(group)
+    p, parts = parts_for_rank(rank, world)
+    acc = np.zeros(m, dtype=np.complex128)
+    for part in parts:
+        acc += np.asarray(partial_fn(part, p), dtype=np.complex128)
+    buf = torch.from_numpy(acc.view(np.float64).copy())
+    if dist.get_backend(group) == "nccl":
+        buf = buf.cuda()
+    dist.all_reduce(buf, op=dist.ReduceOp.SUM, group=group)
+    return buf.cpu().numpy().view(np.complex128).copy()
+
+
+def cut_amplitudes_sharded(circuit, n: int, mask_a: int, z, form: int = 0, group=None) -> np.ndarray:
+    """<z|C|0> for the bit strings z, the branches shared among the ranks of
+    the process group (one GPU per rank)."""
+    from paper_1912_03243_gb300 import sv
+
+    zz = np.ascontiguousarray(z, dtype=np.uint64)
+    return sharded_sum(lambda part, p: sv.sv_cut_amplitudes_part(circuit, n, mask_a, zz, part, p, form)[0], zz.size,
+                       group)

@@ -63,6 +63,8 @@ SIGNATURES = {
     "sv_copy_from_host": (_st, [_vp, _vp, ctypes.c_size_t]),
     "sv_cut_amplitudes": (_st, [ctypes.c_char_p, ctypes.c_int, ctypes.c_uint64, ctypes.c_int, ctypes.c_size_t,
                                 _u64p, _dp, _ip, _vp]),
+    "sv_cut_amplitudes_part": (_st, [ctypes.c_char_p, ctypes.c_int, ctypes.c_uint64, ctypes.c_int, ctypes.c_uint64,
+                                     ctypes.c_int, ctypes.c_size_t, _u64p, _dp, _ip, _vp]),
     "sv_gate_matrix": (ctypes.c_int, [ctypes.c_char_p, _dp, ctypes.c_int, _dp]),
     "sv_version": (ctypes.c_char_p, []),
 }
@@ -157,6 +159,21 @@ def sv_amplitudes_noalloc(state_ptr: int, n: int, dtype: str | int, idx, stream=
                                        ii.ctypes.data_as(_u64p), _dptr(out), _vp(stream)),
            "sv_amplitudes_noalloc")
     return out.view(np.complex128).copy()
+
+
+def sv_cut_amplitudes_part(circuit, n: int, mask_a: int, z, part: int, nparts_log2: int, form: int = 0,
+                           stream=None):
+    """Partial Eq. 3 sum over branches s with s mod 2^nparts_log2 == part."""
+    import torch
+
+    zz = np.ascontiguousarray(z, dtype=np.uint64)
+    out = np.zeros(2 * zz.size, dtype=np.float64)
+    s = ctypes.c_int(0)
+    st = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+    _check(lib().sv_cut_amplitudes_part(_text(circuit), n, ctypes.c_uint64(mask_a), form, ctypes.c_uint64(part),
+                                        nparts_log2, zz.size, zz.ctypes.data_as(_u64p), _dptr(out), ctypes.byref(s),
+                                        _vp(st)), "sv_cut_amplitudes_part")
+    return out.view(np.complex128).copy(), s.value
 
 
 class Plan:

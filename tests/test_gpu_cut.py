@@ -133,3 +133,27 @@ def test_errors(S):
         S.sv_cut_amplitudes(C.ghz_circuit(6), 6, 0, np.array([0], dtype=np.uint64))
     with pytest.raises(S.SVError):
         S.sv_cut_amplitudes(C.ghz_circuit(6), 6, 0b111, np.array([64], dtype=np.uint64))
+
+
+@pytest.mark.parametrize("form", [0, 1])
+def test_parts_add_up(S, orc, form):
+    """Branch sharding: the partial sums over s = part (mod 2^p) for p = 1,
+    2, 3 add up to the full Eq. 3 sum, each part matches the oracle's part,
+    and parts past the branch count are zero."""
+    c = C.grid_circuit(4, 3, 12, 3)
+    mask = C.grid_partition_mask(4, 3, 2)
+    z = np.arange(1 << c.n, dtype=np.uint64)
+    full, s = S.sv_cut_amplitudes(c, c.n, mask, z, form=form)
+    for p in (1, 2, 3):
+        acc = np.zeros_like(full)
+        for part in range(1 << p):
+            got, sp = S.sv_cut_amplitudes_part(c, c.n, mask, z, part, p, form=form)
+            ref, _ = orc.cut_amplitudes_part(c, mask, z, part, p, form=form)
+            assert sp == s
+            close(got, ref, rel=1e-5 * np.max(np.abs(full)) / max(np.max(np.abs(ref)), 1e-300))
+            acc += got
+        close(acc, full)
+    far, _ = S.sv_cut_amplitudes_part(c, c.n, mask, z, (1 << s) + 1, s + 2, form=form)
+    assert np.all(far == 0)
+    with pytest.raises(S.SVError):
+        S.sv_cut_amplitudes_part(c, c.n, mask, z, 4, 2, form=form)
