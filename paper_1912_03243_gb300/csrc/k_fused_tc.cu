@@ -355,9 +355,8 @@ cudaError_t tc_launch(sv_state *h, const TcArgs &args, const void *dA) {
         a.skip_mma = 1;
         a.timeout_ns = 1000000LL;
     }
-    if (!h->d_err) {
-        cudaError_t e = cudaMalloc(&h->d_err, sizeof(int));
-        if (e == cudaSuccess) e = cudaMemset(h->d_err, 0, sizeof(int));
+    {
+        const cudaError_t e = ensure_err_word(h);
         if (e != cudaSuccess) return e;
     }
     const size_t smem = 4 * size_t(kOpBytes) + (size_t(1) << kTcM) * sizeof(float2);

@@ -33,6 +33,13 @@ bool fault_injected(const char *what) {
     return v && std::strcmp(v, what) == 0;
 }
 
+cudaError_t ensure_err_word(sv_state *h) {
+    if (h->d_err) return cudaSuccess;
+    cudaError_t e = cudaMalloc(&h->d_err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(h->d_err, 0, sizeof(int));
+    return e;
+}
+
 sv_status check_launch(cudaError_t e, const char *what) {
     if (fault_injected("launch")) {
         set_error("injected launch failure in %s", what);
@@ -64,7 +71,7 @@ sv_status check_device_error(sv_state *h) {
     SV_CUDA_TRY(cudaMemcpy(&v, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
     if (v == 0) return SV_OK;
     SV_CUDA_TRY(cudaMemset(h->d_err, 0, sizeof(int)));
-    set_error("a device-side wait timed out (tensor-core block); the state is undefined");
+    set_error("a device-side wait timed out; the state is undefined");
     return sv_status(v);
 }
 

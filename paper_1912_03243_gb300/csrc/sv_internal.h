@@ -19,6 +19,9 @@ constexpr int kEncBlock = 1 << kEncBlockLog2;
 void set_error(const char *fmt, ...);
 sv_status cuda_status(cudaError_t e, const char *what);
 bool fault_injected(const char *what);  // SV_FAULT_INJECT host-side hooks
+// Allocate (once) and zero the handle's device error word, which kernels
+// with bounded waits set to SV_ERR_TIMEOUT when a wait gives up.
+cudaError_t ensure_err_word(::sv_state *h);
 // Map a launch result (and the "launch" fault hook) to a status.
 sv_status check_launch(cudaError_t e, const char *what);
 // Synchronise a stream (and honour the "sync" fault hook).

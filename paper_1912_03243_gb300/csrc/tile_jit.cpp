@@ -22,6 +22,7 @@
 // Conditions on thread or CTA index bits become selects, not branches.
 #include <nvrtc.h>
 
+#include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -95,12 +96,28 @@ bool packed_adds_enabled() {
     return !(e && e[0] == '0');
 }
 
-// CTAs per SM the pass kernels are compiled for (register budget); the
-// shared tile (64 KiB) allows up to 3.  SV_TILE_CTAS overrides.
+// Persistent pipelined form (one CTA per SM, two compute groups, three
+// shared tile buffers), emitted with SV_TILE_PIPE=1.  The default is one
+// tile per CTA with two CTAs per SM: the passes are bound by FP32 issue, and
+// the persistent form measured 0-13% slower per pass at 32 qubits (it gains
+// only on light passes of small states).
+bool pipe_enabled() {
+    const char *e = std::getenv("SV_TILE_PIPE");
+    return e && e[0] == '1';
+}
+
+// CTAs per SM the one-tile-per-CTA kernels are compiled for (register
+// budget); the shared tile (64 KiB) allows up to 3.  SV_TILE_CTAS overrides.
 int tile_ctas_per_sm() {
     const char *e = std::getenv("SV_TILE_CTAS");
     const int v = e ? std::atoi(e) : 2;
     return v >= 1 && v <= 3 ? v : 2;
+}
+
+// The pipelined form needs 256-thread groups (2^(m - rb) = 256).
+template <typename R>
+bool pipelined_pass(const TilePlan<R> &tp) {
+    return tp.m - tp.rb == 8 && pipe_enabled();
 }
 
 template <typename R>
@@ -123,26 +140,11 @@ std::string gen_pass(const TilePlan<R> &tp, size_t pass) {
     o << "__device__ __forceinline__ void cpa16(void* s, const void* g) {\n"
          "  u32 sa = (u32)__cvta_generic_to_shared(s);\n"
          "  asm volatile(\"cp.async.cg.shared.global [%0], [%1], 16;\\n\" :: \"r\"(sa), \"l\"(g) : \"memory\");\n}\n";
-    o << "extern \"C\" __global__ void __launch_bounds__(" << G.NT << ", " << tile_ctas_per_sm() << ") svp(" << C2T
-      << "* __restrict__ psi) {\n";
-    o << "  extern __shared__ __align__(16) unsigned char smem[];\n";
-    o << "  " << C2T << "* sm = reinterpret_cast<" << C2T << "*>(smem);\n";
-    o << "  const u32 t = threadIdx.x;\n  const u64 b = blockIdx.x;\n  u64 base = 0;\n";
-    {
-        int pos[kTileMaxOuter];
-        for (int k = 0; k < pa.nouter; ++k) pos[k] = pa.outer_pos[k];
-        emit_deposit(o, "base", "b", pos, pa.nouter, "u64");
-    }
-    // chunk c = t + NT * i: chunk bit k <-> tile bit k + EPC_LOG <-> global tile_pos[k + EPC_LOG]
+    const bool pipe = pipelined_pass(tp);
     const int tbits = G.M - G.RB;  // bits of t
-    {
-        int pos[kTileMaxQ];
-        for (int k = 0; k < tbits; ++k) pos[k] = pa.tile_pos[k + G.EPC_LOG];
-        o << "  u64 g0 = base;\n";
-        emit_deposit(o, "g0", "t", pos, tbits, "u64");
-    }
-    o << "  const u32 s0 = swz(t);\n";
     const int iters = G.NCH / G.NT;
+    const unsigned long long tile_bytes = (1ull << G.M) * 2 * sizeof(R);
+    // chunk c = t + NT * i: chunk bit k <-> tile bit k + EPC_LOG <-> global tile_pos[k + EPC_LOG]
     std::vector<unsigned long long> gi(static_cast<size_t>(iters));
     std::vector<uint32_t> si(static_cast<size_t>(iters));
     for (int i = 0; i < iters; ++i) {
@@ -153,25 +155,110 @@ std::string gen_pass(const TilePlan<R> &tp, size_t pass) {
         gi[size_t(i)] = g;
         si[size_t(i)] = swz_host(c);
     }
-    for (int i = 0; i < iters; ++i)
-        o << "  cpa16(smem + ((s0 ^ " << si[size_t(i)] << "u) << 4), psi + (g0 | " << gi[size_t(i)] << "ull));\n";
-    o << "  asm volatile(\"cp.async.commit_group;\\ncp.async.wait_group 0;\\n\" ::: \"memory\");\n";
-    o << "  __syncthreads();\n";
+    int opos[kTileMaxOuter];
+    for (int k = 0; k < pa.nouter; ++k) opos[k] = pa.outer_pos[k];
+    int tpos[kTileMaxQ];
+    for (int k = 0; k < tbits; ++k) tpos[k] = pa.tile_pos[k + G.EPC_LOG];
+    if (!pipe) {
+        o << "extern \"C\" __global__ void __launch_bounds__(" << G.NT << ", " << tile_ctas_per_sm() << ") svp(" << C2T
+          << "* __restrict__ psi, int* __restrict__ err, u64 timeout_ns, u32 skip_arrive) {\n";
+        o << "  extern __shared__ __align__(16) unsigned char smem[];\n";
+        o << "  " << C2T << "* sm = reinterpret_cast<" << C2T << "*>(smem);\n";
+        o << "  const u32 t = threadIdx.x;\n  const u64 b = blockIdx.x;\n  u64 base = 0;\n";
+        emit_deposit(o, "base", "b", opos, pa.nouter, "u64");
+        o << "  u64 g0 = base;\n";
+        emit_deposit(o, "g0", "t", tpos, tbits, "u64");
+        o << "  const u32 s0 = swz(t);\n";
+        for (int i = 0; i < iters; ++i)
+            o << "  cpa16(smem + ((s0 ^ " << si[size_t(i)] << "u) << 4), psi + (g0 | " << gi[size_t(i)] << "ull));\n";
+        o << "  asm volatile(\"cp.async.commit_group;\\ncp.async.wait_group 0;\\n\" ::: \"memory\");\n";
+        o << "  __syncthreads();\n";
+    } else {
+        // Persistent ring: this CTA's tiles k = 0, 1, ... (tile blockIdx.x +
+        // k gridDim.x) live in buffer k % 3 and are computed by group k % 2.
+        // The group that finishes tile k stores it and then prefetches tile
+        // k + 3 into the freed buffer for the other group; the load's
+        // completion reaches the consumer through mbarrier k % 6 (256
+        // asynchronous arrivals, one per loading thread).  Six barriers, not
+        // three: consecutive phases of a barrier then belong to tiles of the
+        // same group (k and k + 6), so a waiter for phase j has itself seen
+        // phase j - 1 complete, and a parity test cannot mistake an older
+        // open phase for the one it waits for.
+        o << "__device__ __forceinline__ u64 gtimer() { u64 v; asm volatile(\"mov.u64 %0, %%globaltimer;\" : \"=l\"(v)); return v; }\n"
+             "__device__ __forceinline__ u32 mb_try(u32 a, u32 par) { u32 ok; asm volatile(\"{\\n .reg .pred p;\\n "
+             "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\\n selp.u32 %0, 1, 0, p;\\n}\" : \"=r\"(ok) : \"r\"(a), "
+             "\"r\"(par) : \"memory\"); return ok; }\n"
+             "__device__ __forceinline__ u32 grp_any(u32 v, u32 id) { u32 r; asm volatile(\"{\\n .reg .pred p, q;\\n "
+             "setp.ne.u32 p, %1, 0;\\n bar.red.or.pred q, %2, 256, p;\\n selp.u32 %0, 1, 0, q;\\n}\" : \"=r\"(r) : \"r\"(v), "
+             "\"r\"(id) : \"memory\"); return r; }\n"
+             "__device__ __forceinline__ void grp_sync(u32 id) { asm volatile(\"bar.sync %0, 256;\" :: \"r\"(id) : \"memory\"); }\n"
+             "__device__ __forceinline__ u32 wait_phase(u32 a, u32 par, u64 timeout_ns) {\n"
+             "  u32 ok = mb_try(a, par);\n"
+             "  if (!ok) { const u64 t0 = gtimer(); while (!(ok = mb_try(a, par)) && gtimer() - t0 < timeout_ns) {} }\n"
+             "  return ok;\n}\n";
+        o << "__device__ __forceinline__ void load_tile(const " << C2T << "* __restrict__ psi, unsigned char* smem_all, u32 bars, u64 k, "
+             "u64 gt, u32 s0, u32 skip_arrive) {\n";
+        o << "  const u64 tile = blockIdx.x + k * gridDim.x;\n  u64 base = 0;\n";
+        emit_deposit(o, "base", "tile", opos, pa.nouter, "u64");
+        o << "  const u32 bf = (u32)(k % 3ull), bb = (u32)(k % 6ull);\n  unsigned char* buf = smem_all + bf * " << tile_bytes << "u;\n";
+        o << "  const u64 g0 = base | gt;\n";
+        for (int i = 0; i < iters; ++i)
+            o << "  cpa16(buf + ((s0 ^ " << si[size_t(i)] << "u) << 4), psi + (g0 | " << gi[size_t(i)] << "ull));\n";
+        o << "  if (!skip_arrive) asm volatile(\"cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];\" :: \"r\"(bars + 8u * bb) : \"memory\");\n}\n";
+        o << "extern \"C\" __global__ void __launch_bounds__(512, 1) svp(" << C2T
+          << "* __restrict__ psi, int* __restrict__ err, u64 timeout_ns, u32 skip_arrive) {\n";
+        o << "  extern __shared__ __align__(128) unsigned char smem_all[];\n";
+        o << "  const u32 bars = (u32)__cvta_generic_to_shared(smem_all + 3u * " << tile_bytes << "u);\n";
+        o << "  const u32 tid = threadIdx.x, grp = tid >> 8, t = tid & 255u, bid = 1u + grp;\n";
+        o << "  if (tid == 0) {\n    for (u32 i = 0; i < 6; ++i) asm volatile(\"mbarrier.init.shared::cta.b64 [%0], 256;\" :: \"r\"(bars + 8u * i) : \"memory\");\n  }\n";
+        o << "  __syncthreads();\n";
+        o << "  const u64 ntiles = " << (1ull << (pa.n - G.M)) << "ull;\n";
+        o << "  const u64 nk = (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x;\n";
+        o << "  u64 gt = 0;\n";
+        emit_deposit(o, "gt", "t", tpos, tbits, "u64");
+        o << "  const u32 s0 = swz(t);\n";
+        o << "  if (grp == 0) { load_tile(psi, smem_all, bars, 0, gt, s0, skip_arrive); if (nk > 2) load_tile(psi, smem_all, bars, 2, gt, s0, skip_arrive); }\n"
+             "  else if (nk > 1) load_tile(psi, smem_all, bars, 1, gt, s0, skip_arrive);\n";
+        o << "  for (u64 k = grp; k < nk; k += 2) {\n";
+        o << "  const u32 bf = (u32)(k % 3ull), bb = (u32)(k % 6ull), par = (u32)((k / 6ull) & 1ull);\n";
+        o << "  if (grp_any(!wait_phase(bars + 8u * bb, par, timeout_ns), bid)) { if (t == 0) atomicExch(err, 5); "
+             "asm volatile(\"cp.async.wait_all;\" ::: \"memory\"); return; }\n";
+        o << "  unsigned char* smem = smem_all + bf * " << tile_bytes << "u;\n";
+        o << "  " << C2T << "* sm = reinterpret_cast<" << C2T << "*>(smem);\n";
+        o << "  const u64 tile = blockIdx.x + k * gridDim.x;\n  u64 base = 0;\n";
+        emit_deposit(o, "base", "tile", opos, pa.nouter, "u64");
+        o << "  const u64 g0 = base | gt;\n";
+    }
+    const char *SYNC = pipe ? "  grp_sync(bid);\n" : "  __syncthreads();\n";
     o << "  " << RT << " xr[" << G.NR << "], xi[" << G.NR << "];\n  u32 jt = 0, pj = 0;\n";
     (void)0;
 
     int cur_seg = -1;
     uint32_t pv[32] = {0};
-    // Compile-time sign of each register: the stored value is sgn[v] times
-    // the amplitude.  Unconditional sign flips (CZ) only flip sgn; butterflies
-    // fold the signs into add / sub choices; the scatter materialises them.
-    int sgn[32];
-    for (int v = 0; v < 32; ++v) sgn[v] = 1;
-    // Runtime signs: a sign flip conditioned on thread / CTA bits becomes a
-    // per-thread factor sg<c> = cond ? -1 : 1; rsg[v] lists the factors the
-    // stored value still owes.  Butterflies of registers with equal lists
-    // need nothing; otherwise the relative factor enters as an FMA operand.
-    std::vector<int> rsg[32];
+    // The stored value of register v is the amplitude divided by
+    //   sgn[v] * prod(rsg[v]) * 2^(-me[v] / 2):
+    // sgn: compile-time sign (unconditional sign flips such as CZ only flip
+    //   it; butterflies fold it into add / sub choices);
+    // rsg: runtime signs, a sign flip conditioned on thread / CTA bits
+    //   becomes a per-thread factor sg<c> = cond ? -1 : 1 that the register
+    //   still owes (equal lists need nothing in a butterfly, otherwise the
+    //   relative factor enters as an FMA operand);
+    // me: a magnitude exponent.  A phase (+-1 +- i) / sqrt(2) (T and its
+    //   adjoint) is applied as the two additions of (+-1 +- i) and the
+    //   1 / sqrt(2) is owed: the next butterfly on the register takes the
+    //   relative factor 2^((me[v] - me[w]) / 2) as the multiplier of an FMA,
+    //   which costs what the plain addition costs, and a scalar op or the
+    //   scatter pays what is left.
+    // rph: phases conditioned on thread / CTA bits, owed as one per-thread
+    //   complex factor per distinct list (the running product of
+    //   cond ? phase : 1), paid once per register when the register meets
+    //   a register with another list, or at the scatter.
+    int sgn[32], me[32];
+    for (int v = 0; v < 32; ++v) sgn[v] = 1, me[v] = 0;
+    std::vector<int> rsg[32], rph[32];
+    std::map<std::vector<int>, std::pair<std::string, std::string>> cph;  // list -> running product (re, im)
+    std::map<std::pair<std::vector<int>, std::string>, std::pair<std::string, std::string>> kph;  // times a real factor
+    int cph_id = 0;
     std::map<std::vector<int>, std::string> prod_name;
     auto prod = [&](const std::vector<int> &set) -> std::string {  // product of factors (CSE per segment)
         auto it = prod_name.find(set);
@@ -183,6 +270,20 @@ std::string gen_pass(const TilePlan<R> &tp, size_t pass) {
         prod_name.emplace(set, nm);
         return nm;
     };
+    std::map<std::pair<std::string, int>, std::string> scaled_name;
+    // runtime factor f times the compile-time magnitude 2^(d/2) (CSE per segment)
+    auto scaled = [&](const std::string &f, int d) -> std::string {
+        if (d == 0) return f;
+        auto key = std::make_pair(f, d);
+        auto it = scaled_name.find(key);
+        if (it != scaled_name.end()) return it->second;
+        std::string nm = "rs" + std::to_string(scaled_name.size()) + "_" + std::to_string(cur_seg);
+        o << "  const " << RT << " " << nm << " = " << f << " * " << lit(R(std::pow(2.0, d / 2.0)))
+          << ";\n";
+        scaled_name.emplace(key, nm);
+        return nm;
+    };
+    auto mag = [](int d) { return std::pow(2.0, d / 2.0); };
     auto symdiff = [](const std::vector<int> &a, const std::vector<int> &b) {
         std::vector<int> d;
         std::set_symmetric_difference(a.begin(), a.end(), b.begin(), b.end(), std::back_inserter(d));
@@ -191,26 +292,60 @@ std::string gen_pass(const TilePlan<R> &tp, size_t pass) {
     const bool packed = sizeof(R) == 4 && packed_adds_enabled();
     auto reg = [](const char *a, int v) { return std::string(a) + "[" + std::to_string(v) + "]"; };
     auto materialise = [&](int v) {
-        if (!rsg[v].empty()) {
-            const std::string f = prod(rsg[v]);
+        if (!rph[v].empty()) {
+            std::string f;  // real factor ("" for 1)
+            if (!rsg[v].empty()) f = (sgn[v] < 0 ? "-" : "") + scaled(prod(rsg[v]), -me[v]);
+            else if (me[v] != 0 || sgn[v] < 0) f = lit(R(sgn[v] * mag(-me[v])));
+            const auto &c = cph.at(rph[v]);
+            std::pair<std::string, std::string> k = c;
+            if (!f.empty()) {
+                auto key = std::make_pair(rph[v], f);
+                auto it = kph.find(key);
+                if (it == kph.end()) {
+                    const std::string nm = "pk" + std::to_string(cph_id++) + "_" + std::to_string(cur_seg);
+                    o << "  const " << RT << " " << nm << "r = " << c.first << " * " << f << ", " << nm << "i = "
+                      << c.second << " * " << f << ";\n";
+                    it = kph.emplace(key, std::make_pair(nm + "r", nm + "i")).first;
+                }
+                k = it->second;
+            }
+            const std::string x = reg("xr", v), y = reg("xi", v);
+            o << "  { const " << RT << " r = " << x << " * " << k.first << " - " << y << " * " << k.second << "; " << y
+              << " = " << x << " * " << k.second << " + " << y << " * " << k.first << "; " << x << " = r; }\n";
+        } else if (!rsg[v].empty()) {
+            const std::string f = scaled(prod(rsg[v]), -me[v]);
             const char *neg = sgn[v] < 0 ? "-" : "";
             o << "  " << reg("xr", v) << " *= " << neg << f << "; " << reg("xi", v) << " *= " << neg << f << ";\n";
-            rsg[v].clear();
-            sgn[v] = 1;
+        } else if (me[v] != 0) {
+            const std::string f = lit(R(sgn[v] * mag(-me[v])));
+            o << "  " << reg("xr", v) << " *= " << f << "; " << reg("xi", v) << " *= " << f << ";\n";
         } else if (sgn[v] < 0) {
             o << "  " << reg("xr", v) << " = -" << reg("xr", v) << "; " << reg("xi", v) << " = -" << reg("xi", v) << ";\n";
-            sgn[v] = 1;
         }
+        rsg[v].clear();
+        rph[v].clear();
+        sgn[v] = 1;
+        me[v] = 0;
     };
     auto scatter = [&]() {
         for (int v = 0; v < G.NR; ++v) {
-            if (!rsg[v].empty()) materialise(v);
+            if (!rsg[v].empty() || !rph[v].empty() || me[v] != 0) materialise(v);
             const char *neg = sgn[v] < 0 ? "-" : "";
             o << "  sm[pj ^ " << pv[v] << "u] = make_" << C2T << "(" << neg << "xr[" << v << "], " << neg << "xi[" << v
               << "]);\n";
             sgn[v] = 1;
         }
         prod_name.clear();
+        scaled_name.clear();
+        cph.clear();
+        kph.clear();
+    };
+    // x + s * m * y with s = +-1 and multiplier string m ("" for 1): an
+    // addition, or one FMA
+    auto axpy = [&](int sx, const std::string &x, int sy, const std::string &m, const std::string &y) {
+        const std::string nx = sx < 0 ? "-" : "";
+        if (m.empty()) return (sx < 0 ? "-" + x : x) + (sy < 0 ? " - " : " + ") + y;
+        return "fma(" + std::string(sy < 0 ? "-" : "") + m + ", " + y + ", " + nx + x + ")";
     };
     int cond_id = 0;
     for (int i = pa.op_begin; i < pa.op_end; ++i) {
@@ -218,7 +353,7 @@ std::string gen_pass(const TilePlan<R> &tp, size_t pass) {
         if (op.type == TOP_SEG) {
             if (cur_seg >= 0) {
                 scatter();
-                o << "  __syncthreads();\n";
+                o << SYNC;
             }
             cur_seg = op.a;
             const TileSeg &sg = tp.segs[size_t(op.a)];
@@ -252,15 +387,59 @@ std::string gen_pass(const TilePlan<R> &tp, size_t pass) {
             return cond.empty() ? v_new : ("(" + cond + " ? " + v_new + " : " + v_old + ")");
         };
         if (op.type == TOP_SCALE) {
-            const std::string pr = lit(op.u[0]), pi = lit(op.u[1]);
-            for (int v = 0; v < G.NR; ++v)
-                o << "  { " << RT << " r = xr[" << v << "] * " << pr << " - xi[" << v << "] * " << pi << "; xi[" << v
-                  << "] = xr[" << v << "] * " << pi << " + xi[" << v << "] * " << pr << "; xr[" << v << "] = r; }\n";
+            // the scalar, the compile-time sign and the owed magnitude of each
+            // register in one multiplication
+            for (int v = 0; v < G.NR; ++v) {
+                const double f = sgn[v] * mag(-me[v]);
+                const R pr = R(double(op.u[0]) * f), pi = R(double(op.u[1]) * f);
+                const std::string x = reg("xr", v), y = reg("xi", v);
+                if (pi == R(0))
+                    o << "  " << x << " *= " << lit(pr) << "; " << y << " *= " << lit(pr) << ";\n";
+                else if (pr == R(0))
+                    o << "  { const " << RT << " r = " << y << " * " << lit(R(-pi)) << "; " << y << " = " << x << " * "
+                      << lit(pi) << "; " << x << " = r; }\n";
+                else
+                    o << "  { " << RT << " r = " << x << " * " << lit(pr) << " - " << y << " * " << lit(pi) << "; " << y
+                      << " = " << x << " * " << lit(pi) << " + " << y << " * " << lit(pr) << "; " << x << " = r; }\n";
+                sgn[v] = 1;
+                me[v] = 0;
+            }
             continue;
         }
         if (op.type == TOP_PHASE || op.type == TOP_NEG) {
             const uint32_t M = uint32_t(op.a) / 32, V = uint32_t(op.a) % 32;
             const std::string pr = lit(op.u[0]), pi = lit(op.u[1]);
+            // (+-1 +- i) / sqrt(2): two additions, the magnitude is owed
+            const double ar = std::fabs(double(op.u[0])), ai = std::fabs(double(op.u[1]));
+            const bool eighth = cond.empty() && ar > 0.5 && std::fabs(ar - ai) <= 4e-7 * ar &&
+                                std::fabs(ar - std::sqrt(0.5)) <= 4e-7;
+            const int s0 = op.u[0] < 0 ? -1 : 1, s1 = op.u[1] < 0 ? -1 : 1;
+            if (op.type == TOP_PHASE && !cond.empty()) {
+                // per-thread factor; each distinct list of the affected
+                // registers gets its running product once
+                const std::string ph = "ph" + std::to_string(cid);
+                o << "  const " << RT << " " << ph << "r = " << cond << " ? " << RT << "(" << pr << ") : " << RT << "(1), "
+                  << ph << "i = " << cond << " ? " << RT << "(" << pi << ") : " << RT << "(0);\n";
+                for (int v = 0; v < G.NR; ++v) {
+                    if ((uint32_t(v) & M) != V) continue;
+                    std::vector<int> nl = rph[v];
+                    nl.insert(std::lower_bound(nl.begin(), nl.end(), cid), cid);
+                    if (!cph.count(nl)) {
+                        if (rph[v].empty()) {
+                            cph.emplace(nl, std::make_pair(ph + "r", ph + "i"));
+                        } else {
+                            const auto &c = cph.at(rph[v]);
+                            const std::string nm = "pc" + std::to_string(cph_id++) + "_" + std::to_string(cur_seg);
+                            o << "  const " << RT << " " << nm << "r = " << c.first << " * " << ph << "r - " << c.second
+                              << " * " << ph << "i, " << nm << "i = " << c.first << " * " << ph << "i + " << c.second
+                              << " * " << ph << "r;\n";
+                            cph.emplace(nl, std::make_pair(nm + "r", nm + "i"));
+                        }
+                    }
+                    rph[v] = nl;
+                }
+                continue;
+            }
             for (int v = 0; v < G.NR; ++v) {
                 if ((uint32_t(v) & M) != V) continue;
                 const std::string x = "xr[" + std::to_string(v) + "]", y = "xi[" + std::to_string(v) + "]";
@@ -271,6 +450,11 @@ std::string gen_pass(const TilePlan<R> &tp, size_t pass) {
                         auto it = std::lower_bound(r.begin(), r.end(), cid);
                         r.insert(it, cid);
                     }
+                } else if (eighth) {
+                    // (s0 + i s1)(x + i y) = (s0 x - s1 y) + i (s1 x + s0 y)
+                    o << "  { const " << RT << " r = " << axpy(s0, x, -s1, "", y) << "; " << y << " = "
+                      << axpy(s1, x, s0, "", y) << "; " << x << " = r; }\n";
+                    me[v] += 1;
                 } else {
                     o << "  { " << RT << " r = " << x << " * " << pr << " - " << y << " * " << pi << "; " << RT
                       << " q = " << x << " * " << pi << " + " << y << " * " << pr << "; " << x << " = "
@@ -294,17 +478,27 @@ std::string gen_pass(const TilePlan<R> &tp, size_t pass) {
                 materialise(v);
                 materialise(w);
             }
-            const int sa = sgn[v], sb = sgn[w], r = sa * sb;
-            // relative runtime factor of b with respect to a ("" when the lists agree)
-            const std::vector<int> rel = symdiff(rsg[v], rsg[w]);
-            const std::string rf = rel.empty() ? std::string() : prod(rel);
+            if (rph[v] != rph[w]) {  // complex relative factors are paid first
+                materialise(v);
+                materialise(w);
+            }
             if (op.type == TOP_STRUCT && kind == SK_X && cond.empty()) {
                 o << "  { const " << RT << " t0 = " << ar << ", t1 = " << ai << "; " << ar << " = " << br << "; " << ai
                   << " = " << bi << "; " << br << " = t0; " << bi << " = t1; }\n";
                 std::swap(sgn[v], sgn[w]);
                 std::swap(rsg[v], rsg[w]);
+                std::swap(rph[v], rph[w]);
+                std::swap(me[v], me[w]);
                 continue;
             }
+            const int sa = sgn[v], sb = sgn[w], r = sa * sb;
+            // b's stored value times 2^(dm / 2) is on a's magnitude scale
+            const int dm = me[v] - me[w];
+            // relative runtime factor of b with respect to a ("" when the lists agree)
+            const std::vector<int> rel = symdiff(rsg[v], rsg[w]);
+            const std::string rf = rel.empty() ? std::string() : prod(rel);
+            // multiplier of b: runtime factor and magnitude ("" for 1)
+            const std::string mb = rf.empty() ? (dm == 0 ? std::string() : lit(R(mag(dm)))) : scaled(rf, dm);
             if (op.type == TOP_STRUCT && (kind == SK_H || kind == SK_SY || kind == SK_SYD) && cond.empty()) {
                 // true a' = sa (m00 A + m01 r B), b' = sa (m10 A + m11 r B); each is
                 // +-(A + B) or +-(A - B), one of each
@@ -314,18 +508,19 @@ std::string gen_pass(const TilePlan<R> &tp, size_t pass) {
                 sgn[v] = sa * m[0];
                 sgn[w] = sa * m[2];
                 rsg[w] = rsg[v];
-                if (!rf.empty()) {  // A' = A + e rf B, B' = A - e rf B
+                me[w] = me[v];
+                if (!mb.empty()) {  // A' = A + e mb B, B' = A - e mb B
                     const std::string e1 = a_plus ? "" : "-";
                     const std::string e2 = a_plus ? "-" : "";
                     if (packed) {
                         o << "  { const u64 a = pk(" << ar << ", " << ai << "), b = pk(" << br << ", " << bi << "); "
-                          << "upk(fma2(b, pk(" << e1 << rf << ", " << e1 << rf << "), a), " << ar << ", " << ai << "); "
-                          << "upk(fma2(b, pk(" << e2 << rf << ", " << e2 << rf << "), a), " << br << ", " << bi << "); }\n";
+                          << "upk(fma2(b, pk(" << e1 << mb << ", " << e1 << mb << "), a), " << ar << ", " << ai << "); "
+                          << "upk(fma2(b, pk(" << e2 << mb << ", " << e2 << mb << "), a), " << br << ", " << bi << "); }\n";
                     } else {
                         o << "  { const " << RT << " a0 = " << ar << ", a1 = " << ai << ", b0 = " << br << ", b1 = " << bi
-                          << "; " << ar << " = fma(" << e1 << rf << ", b0, a0); " << ai << " = fma(" << e1 << rf
-                          << ", b1, a1); " << br << " = fma(" << e2 << rf << ", b0, a0); " << bi << " = fma(" << e2
-                          << rf << ", b1, a1); }\n";
+                          << "; " << ar << " = fma(" << e1 << mb << ", b0, a0); " << ai << " = fma(" << e1 << mb
+                          << ", b1, a1); " << br << " = fma(" << e2 << mb << ", b0, a0); " << bi << " = fma(" << e2
+                          << mb << ", b1, a1); }\n";
                     }
                     continue;
                 }
@@ -341,18 +536,15 @@ std::string gen_pass(const TilePlan<R> &tp, size_t pass) {
                 }
                 continue;
             }
-            if (op.type == TOP_STRUCT && !rf.empty()) {  // SX / SXD / runtime-conditioned: align b with a
-                o << "  " << br << " *= " << rf << "; " << bi << " *= " << rf << ";\n";
-                rsg[w] = rsg[v];
-            }
             std::string nar, nai, nbr, nbi;
-            const std::string rs = r > 0 ? " + " : " - ", rn = r > 0 ? " - " : " + ";
             if (op.type == TOP_G1) {
-                // signs folded into the constants: a' = u00 sa A + u01 sb B, ...
+                // signs and b's magnitude folded into the constants:
+                // a' = u00 sa A + u01 sb mag B, ...
                 std::string u[8];
                 for (int k = 0; k < 8; ++k) {
-                    const int colsign = (k == 0 || k == 1 || k == 4 || k == 5) ? sa : sb;
-                    u[k] = lit(R(colsign) * op.u[k]);
+                    const bool bcol = !(k == 0 || k == 1 || k == 4 || k == 5);
+                    const double f = bcol ? sb * mag(dm) : sa;
+                    u[k] = lit(R(f * double(op.u[k])));
                 }
                 nar = u[0] + "*ar - " + u[1] + "*ai + " + u[2] + "*br - " + u[3] + "*bi";
                 nai = u[0] + "*ai + " + u[1] + "*ar + " + u[2] + "*bi + " + u[3] + "*br";
@@ -360,21 +552,32 @@ std::string gen_pass(const TilePlan<R> &tp, size_t pass) {
                 nbi = u[4] + "*ai + " + u[5] + "*ar + " + u[6] + "*bi + " + u[7] + "*br";
                 sgn[v] = sgn[w] = 1;
                 rsg[w] = rsg[v];  // equal lists here (else materialised above)
+                me[w] = me[v];
             } else {
-                // stored results relative to sign sa for both outputs
+                // stored results relative to sign sa and magnitude me[v] for
+                // both outputs; the b terms carry the multiplier mb
                 switch (kind) {
-                    case SK_H: nar = "ar" + rs + "br"; nai = "ai" + rs + "bi"; nbr = "ar" + rn + "br"; nbi = "ai" + rn + "bi"; break;
-                    case SK_SY: nar = "ar" + rn + "br"; nai = "ai" + rn + "bi"; nbr = "ar" + rs + "br"; nbi = "ai" + rs + "bi"; break;
-                    case SK_SYD: nar = "ar" + rs + "br"; nai = "ai" + rs + "bi"; nbr = "-ar" + rs + "br"; nbi = "-ai" + rs + "bi"; break;
+                    case SK_H:
+                        nar = axpy(1, "ar", r, mb, "br"); nai = axpy(1, "ai", r, mb, "bi");
+                        nbr = axpy(1, "ar", -r, mb, "br"); nbi = axpy(1, "ai", -r, mb, "bi"); break;
+                    case SK_SY:
+                        nar = axpy(1, "ar", -r, mb, "br"); nai = axpy(1, "ai", -r, mb, "bi");
+                        nbr = axpy(1, "ar", r, mb, "br"); nbi = axpy(1, "ai", r, mb, "bi"); break;
+                    case SK_SYD:
+                        nar = axpy(1, "ar", r, mb, "br"); nai = axpy(1, "ai", r, mb, "bi");
+                        nbr = axpy(-1, "ar", r, mb, "br"); nbi = axpy(-1, "ai", r, mb, "bi"); break;
                     case SK_SX:  // (A - i r B, -i A + r B)
-                        nar = "ar" + rs + "bi"; nai = "ai" + rn + "br"; nbr = "ai" + rs + "br"; nbi = "-ar" + rs + "bi"; break;
+                        nar = axpy(1, "ar", r, mb, "bi"); nai = axpy(1, "ai", -r, mb, "br");
+                        nbr = axpy(1, "ai", r, mb, "br"); nbi = axpy(-1, "ar", r, mb, "bi"); break;
                     case SK_SXD:  // (A + i r B, i A + r B)
-                        nar = "ar" + rn + "bi"; nai = "ai" + rs + "br"; nbr = "-ai" + rs + "br"; nbi = "ar" + rs + "bi"; break;
-                    default:  // X under a runtime condition (signs are +1 here)
+                        nar = axpy(1, "ar", -r, mb, "bi"); nai = axpy(1, "ai", r, mb, "br");
+                        nbr = axpy(-1, "ai", r, mb, "br"); nbi = axpy(1, "ar", r, mb, "bi"); break;
+                    default:  // X under a runtime condition (plain values here)
                         nar = "br"; nai = "bi"; nbr = "ar"; nbi = "ai"; break;
                 }
                 sgn[w] = sa;
                 rsg[w] = rsg[v];
+                me[w] = me[v];
             }
             o << "  { const " << RT << " ar = " << ar << ", ai = " << ai << ", br = " << br << ", bi = " << bi << "; "
               << ar << " = " << sel(nar, "ar") << "; " << ai << " = " << sel(nai, "ai") << "; " << br << " = "
@@ -383,11 +586,23 @@ std::string gen_pass(const TilePlan<R> &tp, size_t pass) {
     }
     if (cur_seg >= 0) {
         scatter();
-        o << "  __syncthreads();\n";
+        o << SYNC;
     }
     for (int i = 0; i < iters; ++i)
         o << "  *reinterpret_cast<int4*>(psi + (g0 | " << gi[size_t(i)] << "ull)) = *reinterpret_cast<const int4*>(smem + ((s0 ^ "
           << si[size_t(i)] << "u) << 4));\n";
+    if (pipe) {
+        // every thread of the group has read the buffer: refill it
+        o << "  grp_sync(bid);\n";
+        // tile k + 3 signals barrier (k + 3) % 6, whose previous phase (tile
+        // k - 3, loaded by this group) must have completed first
+        o << "  if (k + 3 < nk) {\n"
+             "    if (k >= 3 && grp_any(!wait_phase(bars + 8u * (u32)((k + 3) % 6ull), (u32)(((k - 3) / 6ull) & 1ull), timeout_ns), bid)) "
+             "{ if (t == 0) atomicExch(err, 5); asm volatile(\"cp.async.wait_all;\" ::: \"memory\"); return; }\n"
+             "    load_tile(psi, smem_all, bars, k + 3, gt, s0, skip_arrive);\n  }\n";
+        o << "  }\n";
+        o << "  asm volatile(\"cp.async.wait_all;\" ::: \"memory\");\n";
+    }
     o << "}\n";
     return o.str();
 }
@@ -400,6 +615,7 @@ struct JitEntry {
 
 std::mutex g_jit_mu;
 std::unordered_map<std::string, JitEntry> g_jit;  // key: device + source
+std::unordered_map<const void *, bool> g_pipelined;  // compiled function -> persistent pipelined form
 
 std::string compile_cubin(const std::string &src, std::string *err) {
     nvrtcProgram prog;
@@ -407,8 +623,24 @@ std::string compile_cubin(const std::string &src, std::string *err) {
         *err = "nvrtcCreateProgram failed";
         return {};
     }
-    const char *opts[] = {"--gpu-architecture=sm_103a", "--std=c++17"};
-    const nvrtcResult r = nvrtcCompileProgram(prog, 2, opts);
+    // SV_JIT_VERBOSE=1 prints ptxas resource usage (registers, spills) to stderr
+    const char *ve = std::getenv("SV_JIT_VERBOSE");
+    const bool verbose = ve && ve[0] == '1';
+    const char *opts[] = {"--gpu-architecture=sm_103a", "--std=c++17", "--ptxas-options=-v"};
+    const nvrtcResult r = nvrtcCompileProgram(prog, verbose ? 3 : 2, opts);
+    if (verbose && std::getenv("SV_JIT_DUMP")) {  // SV_JIT_DUMP=<file>: append the generated source
+        if (FILE *f = std::fopen(std::getenv("SV_JIT_DUMP"), "a")) {
+            std::fputs(src.c_str(), f);
+            std::fclose(f);
+        }
+    }
+    if (verbose) {
+        size_t n = 0;
+        nvrtcGetProgramLogSize(prog, &n);
+        std::string log(n, '\0');
+        nvrtcGetProgramLog(prog, &log[0]);
+        std::fprintf(stderr, "%s\n", log.c_str());
+    }
     std::string cubin;
     if (r != NVRTC_SUCCESS) {
         size_t n = 0;
@@ -479,13 +711,15 @@ sv_status jit_plan_impl(const TilePlan<R> &tp, std::vector<void *> *fns) {
             cudaError_t ce = cudaLibraryLoadData(&e.lib, cubin[size_t(j)].data(), nullptr, nullptr, 0, nullptr,
                                                  nullptr, 0);
             if (ce == cudaSuccess) ce = cudaLibraryGetKernel(&e.fn, e.lib, "svp");
-            const int smem = (1 << tp.m) * int(2 * sizeof(R));
+            const bool pipe = pipelined_pass(tp);
+            const int smem = (1 << tp.m) * int(2 * sizeof(R)) * (pipe ? 3 : 1) + (pipe ? 64 : 0);
             // a cudaKernel_t is accepted wherever a kernel symbol is
             if (ce == cudaSuccess)
                 ce = cudaFuncSetAttribute(reinterpret_cast<const void *>(e.fn),
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
             if (ce != cudaSuccess) return cuda_status(ce, "loading a compiled pass");
             it = g_jit.emplace(key[size_t(j)], e).first;
+            g_pipelined[reinterpret_cast<const void *>(e.fn)] = pipe;
         }
         (*fns)[size_t(j)] = reinterpret_cast<void *>(it->second.fn);
     }
@@ -518,12 +752,36 @@ const char *tile_kernel_name(const sv_state *h) {
 
 cudaError_t launch_jit_pass(sv_state *h, void *fn, int n, int rb) {
     const int M = h->dt == SV_C64 ? kTileM64 : kTileM128;
-    const int RB = rb;
-    const size_t smem = (size_t(1) << M) * (h->dt == SV_C64 ? 8u : 16u);
+    const size_t tile_bytes = (size_t(1) << M) * (h->dt == SV_C64 ? 8u : 16u);
+    bool pipe = false;
+    {
+        std::lock_guard<std::mutex> lock(g_jit_mu);
+        auto it = g_pipelined.find(fn);
+        if (it != g_pipelined.end()) pipe = it->second;
+    }
+    cudaError_t e = ensure_err_word(h);
+    if (e != cudaSuccess) return e;
     void *psi = h->data;
-    void *args[] = {&psi};
-    return cudaLaunchKernel(static_cast<const void *>(fn), dim3(1u << (n - M)), dim3(1u << (M - RB)), args, smem,
-                            h->stream);
+    int *err = h->d_err;
+    unsigned long long timeout_ns = 2000000000ull;
+    unsigned skip_arrive = 0;
+    if (fault_injected("tile_wait")) {  // test hook: loads never signal, the waits run out after 1 ms
+        skip_arrive = 1;
+        timeout_ns = 1000000ull;
+    }
+    void *args[] = {&psi, &err, &timeout_ns, &skip_arrive};
+    const unsigned long long ntiles = 1ull << (n - M);
+    if (!pipe)
+        return cudaLaunchKernel(static_cast<const void *>(fn), dim3(unsigned(ntiles)), dim3(1u << (M - rb)), args,
+                                tile_bytes, h->stream);
+    static int sms[64] = {0};
+    const int dev = h->device >= 0 && h->device < 64 ? h->device : 0;
+    if (!sms[dev]) {
+        e = cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, h->device);
+        if (e != cudaSuccess) return e;
+    }
+    const unsigned grid = unsigned(std::min<unsigned long long>(ntiles, (unsigned long long)sms[dev]));
+    return cudaLaunchKernel(static_cast<const void *>(fn), dim3(grid), dim3(512), args, 3 * tile_bytes + 64, h->stream);
 }
 
 }  // namespace sv

@@ -438,7 +438,7 @@ sv_status plan_tiles(const std::vector<PGate> &G, int n, const TileConfig &cfg, 
                     op.a = slot | (kind << 8);
                     if (!controlled) scale *= c;
                     out->ops.push_back(op);
-                    if (++since_flush >= 48) flush_scale();
+                    if (++since_flush >= 160) flush_scale();  // bounds the deferred growth at 2^80
                 } else {
                     op.type = TOP_G1;
                     op.a = slot;

@@ -4,6 +4,7 @@
 
 Cases (each a few GB of device memory at most, states larger than L2):
   tiled    28 qubits, random circuit depth 4, tiled passes (compiled kernels)
+  tiled24  28 qubits, random circuit depth 24 (passes as full as at 32 qubits)
   pergate  28 qubits, random circuit depth 1, one launch per gate
   enc      28 qubits, two-byte code, random circuit depth 1
   fused    26 qubits, three dense 6-qubit blocks on the tensor cores
@@ -28,6 +29,9 @@ def main(case: str) -> None:
     if case == "tiled":
         s = sv.StateVector(28, "c64")
         s.run(C.random_circuit(28, 4, 1), "tiled")
+    elif case == "tiled24":
+        s = sv.StateVector(28, "c64")
+        s.run(C.random_circuit(28, 24, 1), "tiled")
     elif case == "pergate":
         s = sv.StateVector(28, "c64")
         s.run(C.random_circuit(28, 1, 1), "pergate")

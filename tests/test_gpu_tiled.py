@@ -45,7 +45,7 @@ def check(dtype, got, ref):
 
 
 @pytest.mark.parametrize("dtype", ["c64", "c128"])
-@pytest.mark.parametrize("n,depth,seed", [(13, 12, 1), (14, 20, 2), (16, 20, 3), (20, 20, 1)])
+@pytest.mark.parametrize("n,depth,seed", [(13, 12, 1), (14, 20, 2), (16, 20, 3), (20, 20, 1), (22, 16, 4)])
 def test_random_circuit(S, orc, dtype, n, depth, seed):
     c = C.random_circuit(n, depth, seed)
     ref = orc.run(c)
@@ -144,3 +144,38 @@ def test_30q_c128_roundtrip(S):
     s.run(C.inverse_circuit(c), "tiled")
     a = s.amplitudes([0, 5, (1 << n) - 1])
     assert abs(a[0] - 1) < 1e-11 and np.max(np.abs(a[1:])) < 1e-11
+
+
+@pytest.mark.parametrize("n", [14, 21])
+def test_one_tile_per_cta_form(S, orc, monkeypatch, n):
+    """SV_TILE_PIPE=1 compiles the persistent form (one CTA per SM, a ring
+    of three tiles); both forms give the oracle's state."""
+    c = C.random_circuit(n, 12, 9)
+    ref = orc.run(c)
+    for pipe in ("0", "1"):
+        monkeypatch.setenv("SV_TILE_PIPE", pipe)
+        s = S.StateVector(n, "c64")
+        s.run(c, "tiled")
+        check("c64", s.to_numpy(), ref)
+
+
+def test_tile_wait_timeout_reports_and_recovers(S, orc, monkeypatch):
+    """The persistent pass (SV_TILE_PIPE=1) waits for each prefetched tile on an mbarrier,
+    bounded by the global timer.  With the host-side hook the loads never
+    signal their barrier; every wait runs out after 1 ms, the groups agree
+    to stop, the kernel sets the error word and returns, and the next
+    synchronising call reports SV_ERR_TIMEOUT with the context still
+    usable."""
+    n = 20
+    c = C.random_circuit(n, 8, 2)
+    s = S.StateVector(n, "c64")
+    monkeypatch.setenv("SV_TILE_PIPE", "1")
+    monkeypatch.setenv("SV_FAULT_INJECT", "tile_wait")
+    with pytest.raises(S.SVError) as e:
+        s.run(c, "tiled")
+        s.sync()
+    assert e.value.status == 5
+    monkeypatch.delenv("SV_FAULT_INJECT")
+    s.set_basis(0)
+    s.run(c, "tiled")
+    check("c64", s.to_numpy(), orc.run(c))
