@@ -100,7 +100,7 @@ struct Half {
 };
 
 sv_status run_half(Half &h, cudaStream_t st, int S, int *derr, std::vector<void *> *fns, TilePlan<float> *tp) {
-    sv_status s = plan_tiles<float>(h.gates, h.nq, TileConfig{kTileM64, tile_rb64(), kTileLow64, true}, tp);
+    sv_status s = plan_tiles<float>(h.gates, h.nq, TileConfig{kTileM64, tile_rb64(), tile_low64(), true}, tp);
     if (s) return s;
     s = jit_tile_plan(*tp, fns);
     if (s) return s;

@@ -85,7 +85,7 @@ sv_status upload_tile_plan(sv_plan_s *p, const TilePlan<R> &tp) {
 sv_status build_tile_plan(sv_state *h, const Circuit &c, sv_plan_s *p) {
     if (h->dt == SV_C64) {
         TilePlan<float> tp;
-        sv_status s = plan_tiles<float>(c, h->n, TileConfig{kTileM64, tile_rb64(), kTileLow64, true}, &tp);
+        sv_status s = plan_tiles<float>(c, h->n, TileConfig{kTileM64, tile_rb64(), tile_low64(), true}, &tp);
         return s ? s : upload_tile_plan(p, tp);
     }
     TilePlan<double> tp;
@@ -251,7 +251,7 @@ sv_status sv_plan_stats(const char *text, int n, sv_dtype dt, int compile, int64
             return SV_ERR_UNSUPPORTED;
         }
         TilePlan<float> tp;
-        s = plan_tiles<float>(c, n, TileConfig{kTileM64, tile_rb64(), kTileLow64, true}, &tp);
+        s = plan_tiles<float>(c, n, TileConfig{kTileM64, tile_rb64(), tile_low64(), true}, &tp);
         return s ? s : count(tp);
     }
     if (n < kTileM128) {

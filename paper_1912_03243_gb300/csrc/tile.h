@@ -129,6 +129,9 @@ sv_status jit_compile_check(const TilePlan<double> &tp);
 // Register bits per thread of complex64 tile passes (SV_TILE_RB overrides,
 // 4 or 5).
 int tile_rb64();
+// Low qubits always in a complex64 tile (contiguous HBM runs of 2^low
+// amplitudes); SV_TILE_LOW overrides (4 to 10).
+int tile_low64();
 // Launch one compiled pass over the whole state (grid = 2^(n-m) CTAs of
 // 2^(m-rb) threads).
 cudaError_t launch_jit_pass(sv_state *h, void *fn, int n, int rb);

@@ -157,6 +157,13 @@ std::string gen_pass(const TilePlan<R> &tp, size_t pass) {
     }
     int opos[kTileMaxOuter];
     for (int k = 0; k < pa.nouter; ++k) opos[k] = pa.outer_pos[k];
+    // global outer-qubit mask -> the same bits of the tile (CTA) number
+    auto compress = [&](unsigned long long g) {
+        unsigned long long c = 0;
+        for (int k = 0; k < pa.nouter; ++k)
+            if (g >> opos[k] & 1) c |= 1ull << k;
+        return c;
+    };
     int tpos[kTileMaxQ];
     for (int k = 0; k < tbits; ++k) tpos[k] = pa.tile_pos[k + G.EPC_LOG];
     if (!pipe) {
@@ -164,13 +171,17 @@ std::string gen_pass(const TilePlan<R> &tp, size_t pass) {
           << "* __restrict__ psi, int* __restrict__ err, u64 timeout_ns, u32 skip_arrive) {\n";
         o << "  extern __shared__ __align__(16) unsigned char smem[];\n";
         o << "  " << C2T << "* sm = reinterpret_cast<" << C2T << "*>(smem);\n";
-        o << "  const u32 t = threadIdx.x;\n  const u64 b = blockIdx.x;\n  u64 base = 0;\n";
-        emit_deposit(o, "base", "b", opos, pa.nouter, "u64");
-        o << "  u64 g0 = base;\n";
+        // the CTA index is the tile number; conditions on outer qubits test
+        // its bits, and the global offsets are recomputed for the store
+        // (short live ranges leave the registers to the amplitudes)
+        o << "  const u32 t = threadIdx.x;\n  const u64 cta = blockIdx.x;\n";
+        o << "  {\n  u64 g0 = 0;\n";
+        emit_deposit(o, "g0", "cta", opos, pa.nouter, "u64");
         emit_deposit(o, "g0", "t", tpos, tbits, "u64");
         o << "  const u32 s0 = swz(t);\n";
         for (int i = 0; i < iters; ++i)
             o << "  cpa16(smem + ((s0 ^ " << si[size_t(i)] << "u) << 4), psi + (g0 | " << gi[size_t(i)] << "ull));\n";
+        o << "  }\n";
         o << "  asm volatile(\"cp.async.commit_group;\\ncp.async.wait_group 0;\\n\" ::: \"memory\");\n";
         o << "  __syncthreads();\n";
     } else {
@@ -225,9 +236,7 @@ std::string gen_pass(const TilePlan<R> &tp, size_t pass) {
              "asm volatile(\"cp.async.wait_all;\" ::: \"memory\"); return; }\n";
         o << "  unsigned char* smem = smem_all + bf * " << tile_bytes << "u;\n";
         o << "  " << C2T << "* sm = reinterpret_cast<" << C2T << "*>(smem);\n";
-        o << "  const u64 tile = blockIdx.x + k * gridDim.x;\n  u64 base = 0;\n";
-        emit_deposit(o, "base", "tile", opos, pa.nouter, "u64");
-        o << "  const u64 g0 = base | gt;\n";
+        o << "  const u64 cta = blockIdx.x + k * gridDim.x;\n";
     }
     const char *SYNC = pipe ? "  grp_sync(bid);\n" : "  __syncthreads();\n";
     o << "  " << RT << " xr[" << G.NR << "], xi[" << G.NR << "];\n  u32 jt = 0, pj = 0;\n";
@@ -379,8 +388,8 @@ std::string gen_pass(const TilePlan<R> &tp, size_t pass) {
         if (op.tmask || op.gmask) {
             cid = cond_id++;
             cond = "c" + std::to_string(cid);
-            o << "  const bool " << cond << " = ((jt & " << op.tmask << "u) == " << op.tval << "u) && ((base & "
-              << op.gmask << "ull) == " << op.gval << "ull);\n";
+            o << "  const bool " << cond << " = ((jt & " << op.tmask << "u) == " << op.tval << "u) && ((cta & "
+              << compress(op.gmask) << "ull) == " << compress(op.gval) << "ull);\n";
             if (op.type == TOP_NEG) o << "  const " << RT << " sg" << cid << " = " << cond << " ? " << RT << "(-1) : " << RT << "(1);\n";
         }
         auto sel = [&](const std::string &v_new, const std::string &v_old) {
@@ -588,9 +597,14 @@ std::string gen_pass(const TilePlan<R> &tp, size_t pass) {
         scatter();
         o << SYNC;
     }
+    o << "  {\n  u64 g0 = " << (pipe ? "gt" : "0") << ";\n";
+    if (!pipe) emit_deposit(o, "g0", "t", tpos, tbits, "u64");
+    emit_deposit(o, "g0", "cta", opos, pa.nouter, "u64");
+    if (!pipe) o << "  const u32 s0 = swz(t);\n";
     for (int i = 0; i < iters; ++i)
         o << "  *reinterpret_cast<int4*>(psi + (g0 | " << gi[size_t(i)] << "ull)) = *reinterpret_cast<const int4*>(smem + ((s0 ^ "
           << si[size_t(i)] << "u) << 4));\n";
+    o << "  }\n";
     if (pipe) {
         // every thread of the group has read the buffer: refill it
         o << "  grp_sync(bid);\n";

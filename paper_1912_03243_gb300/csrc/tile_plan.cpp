@@ -234,6 +234,12 @@ int tile_rb64() {
     return (v == 4 || v == 5) ? v : kTileRB64;
 }
 
+int tile_low64() {
+    const char *e = std::getenv("SV_TILE_LOW");
+    const int v = e ? std::atoi(e) : kTileLow64;
+    return (v >= 4 && v <= 10) ? v : kTileLow64;
+}
+
 template <typename R>
 sv_status plan_tiles(const std::vector<PGate> &G, int n, const TileConfig &cfg, TilePlan<R> *out) {
     out->passes.clear();
