@@ -99,7 +99,7 @@ struct Half {
     float2 *d = nullptr;
 };
 
-sv_status run_half(Half &h, cudaStream_t st, int S, int *derr, std::vector<void *> *fns, TilePlan<float> *tp) {
+sv_status run_half(Half &h, cudaStream_t st, int S, std::vector<void *> *fns, TilePlan<float> *tp) {
     sv_status s = plan_tiles<float>(h.gates, h.nq, TileConfig{kTileM64, tile_rb64(), tile_low64(), true}, tp);
     if (s) return s;
     s = jit_tile_plan(*tp, fns);
@@ -109,7 +109,6 @@ sv_status run_half(Half &h, cudaStream_t st, int S, int *derr, std::vector<void 
     tmp.dt = SV_C64;
     tmp.data = h.d;
     tmp.stream = st;
-    tmp.d_err = derr;
     SV_CUDA_TRY(cudaGetDevice(&tmp.device));
     SV_CUDA_TRY(cudaMemsetAsync(h.d, 0, sizeof(float2) << h.nq, st));
     k_branch_init<<<64, 256, 0, st>>>(h.d, h.nlocal, S);
@@ -120,7 +119,6 @@ sv_status run_half(Half &h, cudaStream_t st, int S, int *derr, std::vector<void 
         if (s) return s;
     }
     tmp.data = nullptr;
-    tmp.d_err = nullptr;
     return SV_OK;
 }
 
@@ -256,7 +254,6 @@ static sv_status cut_impl(const char *text, int n, uint64_t maskA, int form, uin
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     uint64_t *dz = nullptr;
     double2 *dout = nullptr;
-    int *derr = nullptr;  // error word of the bounded waits in the tile passes
     std::vector<uint64_t> zs(2 * m);
     for (size_t j = 0; j < m; ++j) {
         uint64_t za = 0, zb = 0;
@@ -274,14 +271,11 @@ static sv_status cut_impl(const char *text, int n, uint64_t maskA, int form, uin
             if (h.d) cudaFree(h.d);
         if (dz) cudaFree(dz);
         if (dout) cudaFree(dout);
-        if (derr) cudaFree(derr);
     };
     cudaError_t e = cudaMalloc(&half[0].d, bytesA);
     if (e == cudaSuccess) e = cudaMalloc(&half[1].d, bytesB);
     if (e == cudaSuccess) e = cudaMalloc(&dz, bytesZ);
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&dout), bytesO);
-    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&derr), sizeof(int));
-    if (e == cudaSuccess) e = cudaMemsetAsync(derr, 0, sizeof(int), st);
     if (e != cudaSuccess) {
         release();
         return cuda_status(e, "cudaMalloc (decomposition)");
@@ -289,7 +283,7 @@ static sv_status cut_impl(const char *text, int n, uint64_t maskA, int form, uin
     for (int p = 0; p < 2 && s == SV_OK; ++p) {
         std::vector<void *> fns;
         TilePlan<float> tp;
-        s = run_half(half[p], st, Svar, derr, &fns, &tp);
+        s = run_half(half[p], st, Svar, &fns, &tp);
     }
     if (s == SV_OK) {
         e = cudaMemcpyAsync(dz, zs.data(), bytesZ, cudaMemcpyHostToDevice, st);
@@ -307,15 +301,6 @@ static sv_status cut_impl(const char *text, int n, uint64_t maskA, int form, uin
         if (e != cudaSuccess) s = cuda_status(e, "cudaMemcpyAsync");
     }
     if (s == SV_OK) s = sync_stream(st, "sv_cut_amplitudes");
-    if (s == SV_OK) {
-        int v = 0;
-        e = cudaMemcpy(&v, derr, sizeof(int), cudaMemcpyDeviceToHost);
-        if (e != cudaSuccess) s = cuda_status(e, "cudaMemcpy");
-        else if (v != 0) {
-            set_error("a device-side wait timed out in a branch pass");
-            s = sv_status(v);
-        }
-    }
     release();
     return s;
 }

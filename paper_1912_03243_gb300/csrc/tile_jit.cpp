@@ -96,28 +96,12 @@ bool packed_adds_enabled() {
     return !(e && e[0] == '0');
 }
 
-// Persistent pipelined form (one CTA per SM, two compute groups, three
-// shared tile buffers), emitted with SV_TILE_PIPE=1.  The default is one
-// tile per CTA with two CTAs per SM: the passes are bound by FP32 issue, and
-// the persistent form measured 0-13% slower per pass at 32 qubits (it gains
-// only on light passes of small states).
-bool pipe_enabled() {
-    const char *e = std::getenv("SV_TILE_PIPE");
-    return e && e[0] == '1';
-}
-
-// CTAs per SM the one-tile-per-CTA kernels are compiled for (register
-// budget); the shared tile (64 KiB) allows up to 3.  SV_TILE_CTAS overrides.
+// CTAs per SM the pass kernels are compiled for (register budget); the
+// shared tile (64 KiB) allows up to 3.  SV_TILE_CTAS overrides.
 int tile_ctas_per_sm() {
     const char *e = std::getenv("SV_TILE_CTAS");
     const int v = e ? std::atoi(e) : 2;
     return v >= 1 && v <= 3 ? v : 2;
-}
-
-// The pipelined form needs 256-thread groups (2^(m - rb) = 256).
-template <typename R>
-bool pipelined_pass(const TilePlan<R> &tp) {
-    return tp.m - tp.rb == 8 && pipe_enabled();
 }
 
 template <typename R>
@@ -140,7 +124,6 @@ std::string gen_pass(const TilePlan<R> &tp, size_t pass) {
     o << "__device__ __forceinline__ void cpa16(void* s, const void* g) {\n"
          "  u32 sa = (u32)__cvta_generic_to_shared(s);\n"
          "  asm volatile(\"cp.async.cg.shared.global [%0], [%1], 16;\\n\" :: \"r\"(sa), \"l\"(g) : \"memory\");\n}\n";
-    const bool pipe = pipelined_pass(tp);
     const int tbits = G.M - G.RB;  // bits of t
     const int iters = G.NCH / G.NT;
     const unsigned long long tile_bytes = (1ull << G.M) * 2 * sizeof(R);
@@ -166,79 +149,24 @@ std::string gen_pass(const TilePlan<R> &tp, size_t pass) {
     };
     int tpos[kTileMaxQ];
     for (int k = 0; k < tbits; ++k) tpos[k] = pa.tile_pos[k + G.EPC_LOG];
-    if (!pipe) {
-        o << "extern \"C\" __global__ void __launch_bounds__(" << G.NT << ", " << tile_ctas_per_sm() << ") svp(" << C2T
-          << "* __restrict__ psi, int* __restrict__ err, u64 timeout_ns, u32 skip_arrive) {\n";
-        o << "  extern __shared__ __align__(16) unsigned char smem[];\n";
-        o << "  " << C2T << "* sm = reinterpret_cast<" << C2T << "*>(smem);\n";
-        // the CTA index is the tile number; conditions on outer qubits test
-        // its bits, and the global offsets are recomputed for the store
-        // (short live ranges leave the registers to the amplitudes)
-        o << "  const u32 t = threadIdx.x;\n  const u64 cta = blockIdx.x;\n";
-        o << "  {\n  u64 g0 = 0;\n";
-        emit_deposit(o, "g0", "cta", opos, pa.nouter, "u64");
-        emit_deposit(o, "g0", "t", tpos, tbits, "u64");
-        o << "  const u32 s0 = swz(t);\n";
-        for (int i = 0; i < iters; ++i)
-            o << "  cpa16(smem + ((s0 ^ " << si[size_t(i)] << "u) << 4), psi + (g0 | " << gi[size_t(i)] << "ull));\n";
-        o << "  }\n";
-        o << "  asm volatile(\"cp.async.commit_group;\\ncp.async.wait_group 0;\\n\" ::: \"memory\");\n";
-        o << "  __syncthreads();\n";
-    } else {
-        // Persistent ring: this CTA's tiles k = 0, 1, ... (tile blockIdx.x +
-        // k gridDim.x) live in buffer k % 3 and are computed by group k % 2.
-        // The group that finishes tile k stores it and then prefetches tile
-        // k + 3 into the freed buffer for the other group; the load's
-        // completion reaches the consumer through mbarrier k % 6 (256
-        // asynchronous arrivals, one per loading thread).  Six barriers, not
-        // three: consecutive phases of a barrier then belong to tiles of the
-        // same group (k and k + 6), so a waiter for phase j has itself seen
-        // phase j - 1 complete, and a parity test cannot mistake an older
-        // open phase for the one it waits for.
-        o << "__device__ __forceinline__ u64 gtimer() { u64 v; asm volatile(\"mov.u64 %0, %%globaltimer;\" : \"=l\"(v)); return v; }\n"
-             "__device__ __forceinline__ u32 mb_try(u32 a, u32 par) { u32 ok; asm volatile(\"{\\n .reg .pred p;\\n "
-             "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\\n selp.u32 %0, 1, 0, p;\\n}\" : \"=r\"(ok) : \"r\"(a), "
-             "\"r\"(par) : \"memory\"); return ok; }\n"
-             "__device__ __forceinline__ u32 grp_any(u32 v, u32 id) { u32 r; asm volatile(\"{\\n .reg .pred p, q;\\n "
-             "setp.ne.u32 p, %1, 0;\\n bar.red.or.pred q, %2, 256, p;\\n selp.u32 %0, 1, 0, q;\\n}\" : \"=r\"(r) : \"r\"(v), "
-             "\"r\"(id) : \"memory\"); return r; }\n"
-             "__device__ __forceinline__ void grp_sync(u32 id) { asm volatile(\"bar.sync %0, 256;\" :: \"r\"(id) : \"memory\"); }\n"
-             "__device__ __forceinline__ u32 wait_phase(u32 a, u32 par, u64 timeout_ns) {\n"
-             "  u32 ok = mb_try(a, par);\n"
-             "  if (!ok) { const u64 t0 = gtimer(); while (!(ok = mb_try(a, par)) && gtimer() - t0 < timeout_ns) {} }\n"
-             "  return ok;\n}\n";
-        o << "__device__ __forceinline__ void load_tile(const " << C2T << "* __restrict__ psi, unsigned char* smem_all, u32 bars, u64 k, "
-             "u64 gt, u32 s0, u32 skip_arrive) {\n";
-        o << "  const u64 tile = blockIdx.x + k * gridDim.x;\n  u64 base = 0;\n";
-        emit_deposit(o, "base", "tile", opos, pa.nouter, "u64");
-        o << "  const u32 bf = (u32)(k % 3ull), bb = (u32)(k % 6ull);\n  unsigned char* buf = smem_all + bf * " << tile_bytes << "u;\n";
-        o << "  const u64 g0 = base | gt;\n";
-        for (int i = 0; i < iters; ++i)
-            o << "  cpa16(buf + ((s0 ^ " << si[size_t(i)] << "u) << 4), psi + (g0 | " << gi[size_t(i)] << "ull));\n";
-        o << "  if (!skip_arrive) asm volatile(\"cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];\" :: \"r\"(bars + 8u * bb) : \"memory\");\n}\n";
-        o << "extern \"C\" __global__ void __launch_bounds__(512, 1) svp(" << C2T
-          << "* __restrict__ psi, int* __restrict__ err, u64 timeout_ns, u32 skip_arrive) {\n";
-        o << "  extern __shared__ __align__(128) unsigned char smem_all[];\n";
-        o << "  const u32 bars = (u32)__cvta_generic_to_shared(smem_all + 3u * " << tile_bytes << "u);\n";
-        o << "  const u32 tid = threadIdx.x, grp = tid >> 8, t = tid & 255u, bid = 1u + grp;\n";
-        o << "  if (tid == 0) {\n    for (u32 i = 0; i < 6; ++i) asm volatile(\"mbarrier.init.shared::cta.b64 [%0], 256;\" :: \"r\"(bars + 8u * i) : \"memory\");\n  }\n";
-        o << "  __syncthreads();\n";
-        o << "  const u64 ntiles = " << (1ull << (pa.n - G.M)) << "ull;\n";
-        o << "  const u64 nk = (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x;\n";
-        o << "  u64 gt = 0;\n";
-        emit_deposit(o, "gt", "t", tpos, tbits, "u64");
-        o << "  const u32 s0 = swz(t);\n";
-        o << "  if (grp == 0) { load_tile(psi, smem_all, bars, 0, gt, s0, skip_arrive); if (nk > 2) load_tile(psi, smem_all, bars, 2, gt, s0, skip_arrive); }\n"
-             "  else if (nk > 1) load_tile(psi, smem_all, bars, 1, gt, s0, skip_arrive);\n";
-        o << "  for (u64 k = grp; k < nk; k += 2) {\n";
-        o << "  const u32 bf = (u32)(k % 3ull), bb = (u32)(k % 6ull), par = (u32)((k / 6ull) & 1ull);\n";
-        o << "  if (grp_any(!wait_phase(bars + 8u * bb, par, timeout_ns), bid)) { if (t == 0) atomicExch(err, 5); "
-             "asm volatile(\"cp.async.wait_all;\" ::: \"memory\"); return; }\n";
-        o << "  unsigned char* smem = smem_all + bf * " << tile_bytes << "u;\n";
-        o << "  " << C2T << "* sm = reinterpret_cast<" << C2T << "*>(smem);\n";
-        o << "  const u64 cta = blockIdx.x + k * gridDim.x;\n";
-    }
-    const char *SYNC = pipe ? "  grp_sync(bid);\n" : "  __syncthreads();\n";
+    o << "extern \"C\" __global__ void __launch_bounds__(" << G.NT << ", " << tile_ctas_per_sm() << ") svp(" << C2T
+      << "* __restrict__ psi) {\n";
+    o << "  extern __shared__ __align__(16) unsigned char smem[];\n";
+    o << "  " << C2T << "* sm = reinterpret_cast<" << C2T << "*>(smem);\n";
+    // the CTA index is the tile number; conditions on outer qubits test
+    // its bits, and the global offsets are recomputed for the store
+    // (short live ranges leave the registers to the amplitudes)
+    o << "  const u32 t = threadIdx.x;\n  const u64 cta = blockIdx.x;\n";
+    o << "  {\n  u64 g0 = 0;\n";
+    emit_deposit(o, "g0", "cta", opos, pa.nouter, "u64");
+    emit_deposit(o, "g0", "t", tpos, tbits, "u64");
+    o << "  const u32 s0 = swz(t);\n";
+    for (int i = 0; i < iters; ++i)
+        o << "  cpa16(smem + ((s0 ^ " << si[size_t(i)] << "u) << 4), psi + (g0 | " << gi[size_t(i)] << "ull));\n";
+    o << "  }\n";
+    o << "  asm volatile(\"cp.async.commit_group;\\ncp.async.wait_group 0;\\n\" ::: \"memory\");\n";
+    o << "  __syncthreads();\n";
+    const char *SYNC = "  __syncthreads();\n";
     o << "  " << RT << " xr[" << G.NR << "], xi[" << G.NR << "];\n  u32 jt = 0, pj = 0;\n";
     (void)0;
 
@@ -597,26 +525,14 @@ std::string gen_pass(const TilePlan<R> &tp, size_t pass) {
         scatter();
         o << SYNC;
     }
-    o << "  {\n  u64 g0 = " << (pipe ? "gt" : "0") << ";\n";
-    if (!pipe) emit_deposit(o, "g0", "t", tpos, tbits, "u64");
+    o << "  {\n  u64 g0 = 0;\n";
+    emit_deposit(o, "g0", "t", tpos, tbits, "u64");
     emit_deposit(o, "g0", "cta", opos, pa.nouter, "u64");
-    if (!pipe) o << "  const u32 s0 = swz(t);\n";
+    o << "  const u32 s0 = swz(t);\n";
     for (int i = 0; i < iters; ++i)
         o << "  *reinterpret_cast<int4*>(psi + (g0 | " << gi[size_t(i)] << "ull)) = *reinterpret_cast<const int4*>(smem + ((s0 ^ "
           << si[size_t(i)] << "u) << 4));\n";
     o << "  }\n";
-    if (pipe) {
-        // every thread of the group has read the buffer: refill it
-        o << "  grp_sync(bid);\n";
-        // tile k + 3 signals barrier (k + 3) % 6, whose previous phase (tile
-        // k - 3, loaded by this group) must have completed first
-        o << "  if (k + 3 < nk) {\n"
-             "    if (k >= 3 && grp_any(!wait_phase(bars + 8u * (u32)((k + 3) % 6ull), (u32)(((k - 3) / 6ull) & 1ull), timeout_ns), bid)) "
-             "{ if (t == 0) atomicExch(err, 5); asm volatile(\"cp.async.wait_all;\" ::: \"memory\"); return; }\n"
-             "    load_tile(psi, smem_all, bars, k + 3, gt, s0, skip_arrive);\n  }\n";
-        o << "  }\n";
-        o << "  asm volatile(\"cp.async.wait_all;\" ::: \"memory\");\n";
-    }
     o << "}\n";
     return o.str();
 }
@@ -629,7 +545,6 @@ struct JitEntry {
 
 std::mutex g_jit_mu;
 std::unordered_map<std::string, JitEntry> g_jit;  // key: device + source
-std::unordered_map<const void *, bool> g_pipelined;  // compiled function -> persistent pipelined form
 
 std::string compile_cubin(const std::string &src, std::string *err) {
     nvrtcProgram prog;
@@ -725,15 +640,13 @@ sv_status jit_plan_impl(const TilePlan<R> &tp, std::vector<void *> *fns) {
             cudaError_t ce = cudaLibraryLoadData(&e.lib, cubin[size_t(j)].data(), nullptr, nullptr, 0, nullptr,
                                                  nullptr, 0);
             if (ce == cudaSuccess) ce = cudaLibraryGetKernel(&e.fn, e.lib, "svp");
-            const bool pipe = pipelined_pass(tp);
-            const int smem = (1 << tp.m) * int(2 * sizeof(R)) * (pipe ? 3 : 1) + (pipe ? 64 : 0);
+            const int smem = (1 << tp.m) * int(2 * sizeof(R));
             // a cudaKernel_t is accepted wherever a kernel symbol is
             if (ce == cudaSuccess)
                 ce = cudaFuncSetAttribute(reinterpret_cast<const void *>(e.fn),
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
             if (ce != cudaSuccess) return cuda_status(ce, "loading a compiled pass");
             it = g_jit.emplace(key[size_t(j)], e).first;
-            g_pipelined[reinterpret_cast<const void *>(e.fn)] = pipe;
         }
         (*fns)[size_t(j)] = reinterpret_cast<void *>(it->second.fn);
     }
@@ -767,35 +680,10 @@ const char *tile_kernel_name(const sv_state *h) {
 cudaError_t launch_jit_pass(sv_state *h, void *fn, int n, int rb) {
     const int M = h->dt == SV_C64 ? kTileM64 : kTileM128;
     const size_t tile_bytes = (size_t(1) << M) * (h->dt == SV_C64 ? 8u : 16u);
-    bool pipe = false;
-    {
-        std::lock_guard<std::mutex> lock(g_jit_mu);
-        auto it = g_pipelined.find(fn);
-        if (it != g_pipelined.end()) pipe = it->second;
-    }
-    cudaError_t e = ensure_err_word(h);
-    if (e != cudaSuccess) return e;
     void *psi = h->data;
-    int *err = h->d_err;
-    unsigned long long timeout_ns = 2000000000ull;
-    unsigned skip_arrive = 0;
-    if (fault_injected("tile_wait")) {  // test hook: loads never signal, the waits run out after 1 ms
-        skip_arrive = 1;
-        timeout_ns = 1000000ull;
-    }
-    void *args[] = {&psi, &err, &timeout_ns, &skip_arrive};
-    const unsigned long long ntiles = 1ull << (n - M);
-    if (!pipe)
-        return cudaLaunchKernel(static_cast<const void *>(fn), dim3(unsigned(ntiles)), dim3(1u << (M - rb)), args,
-                                tile_bytes, h->stream);
-    static int sms[64] = {0};
-    const int dev = h->device >= 0 && h->device < 64 ? h->device : 0;
-    if (!sms[dev]) {
-        e = cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, h->device);
-        if (e != cudaSuccess) return e;
-    }
-    const unsigned grid = unsigned(std::min<unsigned long long>(ntiles, (unsigned long long)sms[dev]));
-    return cudaLaunchKernel(static_cast<const void *>(fn), dim3(grid), dim3(512), args, 3 * tile_bytes + 64, h->stream);
+    void *args[] = {&psi};
+    return cudaLaunchKernel(static_cast<const void *>(fn), dim3(1u << (n - M)), dim3(1u << (M - rb)), args, tile_bytes,
+                            h->stream);
 }
 
 }  // namespace sv
