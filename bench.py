@@ -291,6 +291,20 @@ def time_plan(S, state, plan, steps, warmup, world, with_events=True):
     return max_over_ranks(world, t), per_launch
 
 
+# FP32 lane operations per amplitude a gate needs at least: a structured
+# 2x2 (entries 0, +-1, +-i up to one scalar) is one real addition per
+# component and amplitude; T / Tdg multiply half the amplitudes by
+# (1 +- i) / sqrt(2), two additions each; P and CP a complex product (4) on
+# half / a quarter of them; X, Y, Z, S, CX, CZ and SWAP are signs and swaps;
+# anything else (U) is a dense 2x2, 8.
+FP32_OPS = {"H": 2, "SX": 2, "SXDG": 2, "SY": 2, "SYDG": 2, "T": 1, "TDG": 1, "P": 2, "CP": 1,
+            "X": 0, "Y": 0, "Z": 0, "S": 0, "SDG": 0, "CX": 0, "CNOT": 0, "CZ": 0, "SWAP": 0}
+
+
+def fp32_ops_per_amplitude(circ) -> int:
+    return sum(FP32_OPS.get(name.upper(), 8) for name, _, _ in circ.gates)
+
+
 def dominant_roofline(info, per_launch, steps, peak, peak_kind, n=None):
     tot, cnt, byt = {}, {}, {}
     for k in range(steps):
@@ -416,6 +430,22 @@ def run_ours(args, world, rank, local):
                 "bytes_per_launch": byt[dom] / cnt[dom], "peak_kind": peak_kind,
                 "frac_of_nominal_8tbs": achieved / 8000.0,
                 "share_of_step": tot[dom] / sum(tot.values())}
+
+    # The tiled passes are bound by FP32 arithmetic more than by HBM: the
+    # same launches against the FP32 lanes (152 SMs x 128 lanes x SM clock)
+    # with the algorithmic operations the gates need.
+    roofline_fp32 = None
+    if mode == "tiled":
+        ops = fp32_ops_per_amplitude(circ) * (1 << args.n) * args.steps
+        secs = sum(tot.values()) / 1e3
+        mhz = clocks.get("sm_mhz") or 2070.0
+        peak_ops = 152 * 128 * mhz * 1e6
+        roofline_fp32 = {"bound": "alu", "achieved": ops / secs / 1e12, "peak": peak_ops / 1e12,
+                         "unit": "T FP32 lane-ops/s", "frac": ops / secs / peak_ops,
+                         "ops_per_amplitude": fp32_ops_per_amplitude(circ),
+                         "note": "2 per amplitude for each H/SX/SY (one addition per real component), 1 for T "
+                                 "(two additions on half the amplitudes), 0 for CZ; peak at the sampled SM clock"}
+        roofline["fp32"] = roofline_fp32
 
     # accuracy: the circuit followed by its inverse returns |0...0>
     inv = state.plan(C.inverse_circuit(circ), mode)
