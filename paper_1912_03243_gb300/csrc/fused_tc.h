@@ -8,7 +8,8 @@
 
 namespace sv {
 
-constexpr int kTcM = 13;                            // tile bits (2^13 amplitudes per tile)
+constexpr int kTcM = 12;                            // tile bits (2^12 amplitudes per tile)
+constexpr int kTcN = 1 << (kTcM - 6);               // B columns per tile (2^(kTcM + 1) reals / 128)
 constexpr size_t kTcOperandBytes = 2 * 128 * 128 * 2;  // A hi + A lo, BF16 (64 KiB)
 
 struct TcArgs {
@@ -22,7 +23,7 @@ struct TcArgs {
     uint8_t outer_pos[40];
     uint16_t offL[64];            // tile index offset of block-local index l
     uint16_t offP[64];            // tile index offset of pack p
-    uint16_t offN[128];           // tile index offset of column n
+    uint16_t offN[kTcN];          // tile index offset of column n
 };
 
 // Build the BF16 hi/lo operand image of block U (a_ops: 2 * 128 * 128

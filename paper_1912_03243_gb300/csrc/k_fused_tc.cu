@@ -12,14 +12,18 @@
 // Al = bf16(A - Ah)); D = Ah Bh + Ah Bl + Al Bh accumulates in FP32 in tensor
 // memory (relative error about 2^-16 per product instead of 2^-8).
 //
-// Per CTA (persistent, one per SM, 256 threads) and per tile of 2^13
-// amplitudes (the k block qubits plus the lowest other qubits):
-//   cp.async the tile into shared memory (FP32, swizzled) -> convert to Bh, Bl in the
-//   K-major no-swizzle canonical layout -> one thread issues 3 x 8
-//   tcgen05.mma (K = 16 each) into a 128-column TMEM accumulator and commits
-//   to an mbarrier -> all threads wait (bounded by %globaltimer) -> each warp
-//   reads its 32 TMEM lanes with tcgen05.ld and scatters FP32 results back to
-//   the shared tile -> coalesced 16-byte stores to HBM.
+// Per CTA (persistent, one per SM, two groups of 256 threads that share A
+// and otherwise work like separate CTAs: own B, staging tile, TMEM columns,
+// mbarrier and named barrier) and per tile of 2^12 amplitudes (the k block
+// qubits plus the lowest other qubits; B is 128 x 64):
+//   cp.async the tile into the group's staging tile (FP32, swizzled) ->
+//   convert to Bh, Bl in the K-major no-swizzle canonical layout -> one
+//   thread issues 3 x 8 tcgen05.mma (M = 128, N = 64, K = 16 each) into the
+//   group's 64 TMEM columns and commits to its mbarrier -> the group waits
+//   (bounded by %globaltimer) -> each warp reads its 32 TMEM lanes with
+//   tcgen05.ld and scatters FP32 results back to the staging tile ->
+//   coalesced 16-byte stores to HBM.  The groups' phases interleave: some
+//   convert or read back while others wait for memory or for their MMAs.
 // Operand layout (both K-major, no swizzle): element (row, kk) at byte
 // (row%8)*16 + (kk%8)*2 + (kk/8)*128 + (row/8)*2048; leading-dimension byte
 // offset 128 (next 8 K-elements), stride-dimension byte offset 2048 (next 8
@@ -35,9 +39,14 @@
 namespace sv {
 namespace {
 
-constexpr int kTcThreads = 256;
-constexpr int kTcCols = 128;      // TMEM columns of the accumulator (N)
-constexpr uint32_t kOpBytes = 128 * 128 * 2;  // one BF16 operand (32 KiB)
+constexpr int kTcGroup = 256;                  // threads of one group
+constexpr int kTcGroups = 2;                   // groups (tiles in flight) per CTA
+constexpr int kTcThreads = kTcGroups * kTcGroup;
+constexpr int kTcCols = kTcGroups * kTcN;      // TMEM columns: one N-column accumulator per group
+constexpr uint32_t kOpBytes = 128 * 128 * 2;   // one BF16 A operand (32 KiB)
+constexpr uint32_t kBBytes = kTcN * 128 * 2;   // one BF16 B operand (16 KiB)
+constexpr uint32_t kStageBytes = (1u << kTcM) * 8;  // one FP32 staging tile (32 KiB)
+constexpr int kChunkIters = (1 << kTcM) / 2 / kTcGroup;  // 16-byte chunks per thread and tile
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return uint32_t(__cvta_generic_to_shared(p)); }
 
@@ -47,6 +56,8 @@ __device__ __forceinline__ void cp_async16(uint32_t saddr, const void *g) {
 __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
+// barrier of one 256-thread group (named barrier 1 + g)
+__device__ __forceinline__ void group_sync(int g) { asm volatile("bar.sync %0, 256;\n" ::"r"(1 + g) : "memory"); }
 
 // Staging tile layout: 16-byte chunk c (amplitudes 2c, 2c+1) lives at chunk
 // c ^ ((c>>3 ^ c>>6 ^ c>>9) & 7), which spreads both the B-operand reads
@@ -73,8 +84,8 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t
 
 // Instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16
 // (bits 7-9 = 1, 10-12 = 1), both K-major, N >> 3 at bits 17-22, M >> 4 at
-// bits 24-28.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+// bits 24-28 (M = 128, N = kTcN).
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t(kTcN) >> 3) << 17) | ((128u >> 4) << 24);
 
 __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accum) {
     asm volatile(
@@ -84,60 +95,86 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64
         : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
-    uint32_t r[32];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
+// kTcN / 2 consecutive columns of this warp's 32 lanes
+__device__ __forceinline__ void tmem_ld_half(uint32_t taddr, float *v) {
+    static_assert(kTcN == 32 || kTcN == 64, "read-back written for 32 or 64 accumulator columns");
+    uint32_t r[kTcN / 2];
+    if constexpr (kTcN == 32) {
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+            : "r"(taddr));
+    } else {
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+              "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+              "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+            : "r"(taddr));
+    }
     asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 #pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+    for (int i = 0; i < kTcN / 2; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 __global__ void __launch_bounds__(kTcThreads, 1) k_fused_tc(float2 *__restrict__ psi, const uint4 *__restrict__ gA,
                                                             int *__restrict__ err, const TcArgs a) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    unsigned char *sAh = smem, *sAl = smem + kOpBytes;
-    unsigned char *sBh = smem + 2 * kOpBytes, *sBl = smem + 3 * kOpBytes;
-    float2 *sX = reinterpret_cast<float2 *>(smem + 4 * kOpBytes);  // 2^13 amplitudes (64 KiB)
-    __shared__ __align__(8) uint64_t mbar;
+    __shared__ __align__(8) uint64_t mbar[kTcGroups];
     __shared__ uint32_t tmem_slot;
-    __shared__ int abort_flag;
+    __shared__ int abort_flag[kTcGroups];
     // index tables in shared memory: lanes read different entries (a kernel-
     // parameter array would serialise on the constant cache)
-    __shared__ uint16_t tL[64], tP[64], tN[128];   // swizzled staging offsets of l, p, n
-    __shared__ uint64_t gHi[16];                    // global offset of chunk bits 8..11
-    __shared__ uint16_t sHi[16];                    // swizzled chunk of chunk bits 8..11
+    __shared__ uint16_t tL[64], tP[64], tN[kTcN];          // swizzled staging offsets of l, p, n
+    __shared__ uint16_t tK[64];                            // offset of K elements 2i, 2i + 1 (one amplitude)
+    __shared__ uint64_t tB[4][256];                        // global offset of each byte of the tile number
+    __shared__ uint64_t gHi[kChunkIters];                  // global offset of the chunk bits above 7
+    __shared__ uint16_t sHi[kChunkIters];                  // swizzled chunk of the chunk bits above 7
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const uint32_t mbar_a = smem_u32(&mbar);
+    const int g = tid / kTcGroup, lt = tid % kTcGroup, gw = warp & 7;  // group, thread and warp in the group
+    unsigned char *sAh = smem, *sAl = smem + kOpBytes;
+    unsigned char *gbase = smem + 2 * kOpBytes + size_t(g) * (2 * kBBytes + kStageBytes);
+    unsigned char *sBh = gbase, *sBl = gbase + kBBytes;
+    float2 *sX = reinterpret_cast<float2 *>(gbase + 2 * kBBytes);  // 2^kTcM amplitudes
+    const uint32_t mbar_a = smem_u32(&mbar[g]);
 
-    for (int i = tid; i < 128; i += kTcThreads) {
-        tN[i] = uint16_t(sxpos(a.offN[i]));
-        if (i < 64) {
-            tL[i] = uint16_t(sxpos(a.offL[i]));
-            tP[i] = uint16_t(sxpos(a.offP[i]));
+    for (int i = tid; i < 64; i += kTcThreads) {
+        if (i < kTcN) tN[i] = uint16_t(sxpos(a.offN[i]));
+        tL[i] = uint16_t(sxpos(a.offL[i]));
+        tP[i] = uint16_t(sxpos(a.offP[i]));
+        {  // K elements 2i, 2i + 1
+            const int kk = 2 * i, klg = a.k + 1, rm = (2 << a.k) - 1;
+            tK[i] = uint16_t(sxpos(a.offL[(kk & rm) >> 1] ^ a.offP[kk >> klg]));
         }
-        if (i < 16) {  // chunk c = tid + 256 i: tile index bits 9..12 of j = 2c
+        if (i < kChunkIters) {  // chunk c = lt + 256 i: tile index bits 9.. of j = 2c
             const uint32_t j = uint32_t(i) << 9;
-            uint64_t g = 0;
+            uint64_t gg = 0;
             for (int q = 0; q < kTcM; ++q)
-                if (j >> q & 1) g |= uint64_t(1) << a.tile_pos[q];
-            gHi[i] = g;
+                if (j >> q & 1) gg |= uint64_t(1) << a.tile_pos[q];
+            gHi[i] = gg;
             sHi[i] = uint16_t(swz(uint32_t(i) << 8));
         }
+    }
+    // the tile number's outer bits, one table per byte (tile numbers < 2^32)
+    for (int i = tid; i < 4 * 256; i += kTcThreads) {
+        const int byte = i >> 8, v = i & 255;
+        uint64_t off = 0;
+        for (int b = 0; b < 8; ++b) {
+            const int q = 8 * byte + b;
+            if ((v >> b & 1) && q < a.nouter) off |= uint64_t(1) << a.outer_pos[q];
+        }
+        tB[byte][v] = off;
     }
     // this thread's chunk bits 0..7 (tile index bits 1..8)
     uint64_t gLo = 0;
     for (int q = 1; q <= 8; ++q)
-        if ((uint32_t(tid) << 1) >> q & 1) gLo |= uint64_t(1) << a.tile_pos[q];
-    const uint32_t sLo = swz(uint32_t(tid));
-    if (tid == 0) {
-        abort_flag = 0;
+        if ((uint32_t(lt) << 1) >> q & 1) gLo |= uint64_t(1) << a.tile_pos[q];
+    const uint32_t sLo = swz(uint32_t(lt));
+    if (lt == 0) {
+        abort_flag[g] = 0;
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mbar_a) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
@@ -153,30 +190,39 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fused_tc(float2 *__restrict__
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-    const uint32_t tmem = tmem_slot;
+    const uint32_t tmem = tmem_slot + uint32_t(g * kTcN);  // this group's accumulator columns
+    const int klog = a.k + 1, rmask = (2 << a.k) - 1;        // 2d = 2^(k+1)
+    // K element kk = 2i, 2i + 1 (re, im of one amplitude): pack p = kk >> klog,
+    // real row r = kk & rmask (tables written before the barrier above)
+    // per-thread constants of the convert (B row) and of the read-back (D row)
+    const uint32_t sn = tN[lt & (kTcN - 1)];
+    const int drow = 32 * (gw & 3) + lane;
+    const uint32_t srow = tL[(drow & rmask) >> 1] ^ tP[drow >> klog];
+    const int dcomp = drow & 1;
 
     uint32_t phase = 0;
-    for (uint64_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
-        uint64_t base = 0;
-        for (int q = 0; q < a.nouter; ++q) base |= ((tile >> q) & 1ull) << a.outer_pos[q];
-        // load: 16-byte chunks c = tid + 256 i (2 amplitudes, tile index 2c);
+    const uint64_t stride = uint64_t(kTcGroups) * gridDim.x;
+    for (uint64_t tile = uint64_t(kTcGroups) * blockIdx.x + uint64_t(g); tile < a.ntiles; tile += stride) {
+        const uint64_t base = tB[0][tile & 255] | tB[1][(tile >> 8) & 255] | tB[2][(tile >> 16) & 255] |
+                              tB[3][(tile >> 24) & 255];
+        // load: 16-byte chunks c = lt + 256 i (2 amplitudes, tile index 2c);
         // offsets split into a per-thread and a per-i part (disjoint bits)
 #pragma unroll
-        for (int i = 0; i < 16; ++i)
+        for (int i = 0; i < kChunkIters; ++i)
             cp_async16(smem_u32(sX + 2 * (sLo ^ sHi[i])), psi + (base | gLo | gHi[i]));
         cp_async_wait_all();
-        __syncthreads();
-        // convert: one task = one B row n and 8 consecutive K elements (16 B of Bh and of Bl)
-        const int klog = a.k + 1, rmask = (2 << a.k) - 1;  // 2d = 2^(k+1)
-        for (int t = tid; t < 16 * 128; t += kTcThreads) {
-            const int nrow = t & 127, q8 = t >> 7;
-            const uint32_t sn = tN[nrow];
+        group_sync(g);
+        // convert: one task = one B row n and 8 consecutive K elements (16 B
+        // of Bh and of Bl); a thread's row n = lt % kTcN is the same in all
+        // its tasks
+        static_assert(kTcGroup % kTcN == 0, "fixed B row per thread");
+#pragma unroll
+        for (int t = lt; t < 16 * kTcN; t += kTcGroup) {
+            const int nrow = t & (kTcN - 1), q8 = t / kTcN;
             uint32_t hw[4], lw[4];
 #pragma unroll
             for (int e = 0; e < 8; e += 2) {  // elements kk, kk+1: re and im of one amplitude
-                const int kk = q8 * 8 + e;
-                const int p = kk >> klog, r = kk & rmask;
-                const float2 amp = sX[sn ^ tL[r >> 1] ^ tP[p]];
+                const float2 amp = sX[sn ^ tK[q8 * 4 + (e >> 1)]];
                 const __nv_bfloat162 hi = __float22bfloat162_rn(amp);
                 const float2 hf = __bfloat1622float2(hi);
                 const __nv_bfloat162 lo = __float22bfloat162_rn(make_float2(amp.x - hf.x, amp.y - hf.y));
@@ -189,8 +235,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fused_tc(float2 *__restrict__
         }
         // generic-proxy writes -> async proxy (the tensor core reads them)
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-        __syncthreads();
-        if (tid == 0 && !a.skip_mma) {
+        group_sync(g);
+        if (lt == 0 && !a.skip_mma) {
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
             const uint32_t ah = smem_u32(sAh), al = smem_u32(sAl), bh = smem_u32(sBh), bl = smem_u32(sBl);
             uint32_t acc = 0;
@@ -217,45 +263,42 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fused_tc(float2 *__restrict__
                     : "r"(mbar_a), "r"(phase)
                     : "memory");
                 if (!done && globaltimer() - t0 > uint64_t(a.timeout_ns)) {
-                    abort_flag = 1;
+                    abort_flag[g] = 1;
                     break;
                 }
             }
         }
-        __syncthreads();
-        if (abort_flag) break;
+        group_sync(g);
+        if (abort_flag[g]) break;
         phase ^= 1u;
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-        // read D: warp w reads lanes 32 (w % 4) .. +31, columns 64 (w / 4) .. +63
+        // read D: warp gw of the group reads lanes 32 (gw % 4) .. +31 and
+        // half of the columns (a warp reaches the lanes 32 (warp % 4) .. +31;
+        // warp % 4 = gw % 4)
         {
-            const int row = 32 * (warp & 3) + lane;
-            const int p = row >> klog, r = row & rmask;
-            const uint32_t srow = tL[r >> 1] ^ tP[p];
             float *sXf = reinterpret_cast<float *>(sX);
+            const int c0 = (kTcN / 2) * (gw >> 2);
+            float v[kTcN / 2];
+            tmem_ld_half(tmem + (uint32_t(32 * (gw & 3)) << 16) + uint32_t(c0), v);
 #pragma unroll
-            for (int half = 0; half < 2; ++half) {
-                const int c0 = 64 * (warp >> 2) + 32 * half;
-                float v[32];
-                tmem_ld32(tmem + (uint32_t(32 * (warp & 3)) << 16) + uint32_t(c0), v);
-#pragma unroll
-                for (int i = 0; i < 32; ++i) sXf[2 * (srow ^ tN[c0 + i]) + (r & 1)] = v[i];
-            }
+            for (int i = 0; i < kTcN / 2; ++i) sXf[2 * (srow ^ tN[c0 + i]) + dcomp] = v[i];
         }
         asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-        __syncthreads();
+        group_sync(g);
         // store
 #pragma unroll
-        for (int i = 0; i < 16; ++i)
+        for (int i = 0; i < kChunkIters; ++i)
             *reinterpret_cast<float4 *>(psi + (base | gLo | gHi[i])) =
                 *reinterpret_cast<const float4 *>(sX + 2 * (sLo ^ sHi[i]));
-        __syncthreads();
+        group_sync(g);
     }
-    if (abort_flag && tid == 0) atomicExch(err, int(SV_ERR_TIMEOUT));
+    if (abort_flag[g] && lt == 0) atomicExch(err, int(SV_ERR_TIMEOUT));
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
     if (warp == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTcCols) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem_slot), "r"(kTcCols)
+                     : "memory");
     }
 }
 
@@ -339,9 +382,9 @@ void tc_prepare(int n, int k, const int *qubits, const double *U, uint16_t *a_op
             if (p >> i & 1) off |= 1u << gbits[i];
         a.offP[p] = uint16_t(off);
     }
-    for (int nn = 0; nn < 128; ++nn) {
+    for (int nn = 0; nn < kTcN; ++nn) {  // the remaining kTcM - 6 group bits
         uint32_t off = 0;
-        for (int i = 0; i < 7; ++i)
+        for (int i = 0; i < kTcM - 6; ++i)
             if (nn >> i & 1) off |= 1u << gbits[plog + i];
         a.offN[nn] = uint16_t(off);
     }
@@ -359,7 +402,7 @@ cudaError_t tc_launch(sv_state *h, const TcArgs &args, const void *dA) {
         const cudaError_t e = ensure_err_word(h);
         if (e != cudaSuccess) return e;
     }
-    const size_t smem = 4 * size_t(kOpBytes) + (size_t(1) << kTcM) * sizeof(float2);
+    const size_t smem = 2 * size_t(kOpBytes) + kTcGroups * (2 * size_t(kBBytes) + size_t(kStageBytes));
     static bool configured = false;
     if (!configured) {
         const cudaError_t e = cudaFuncSetAttribute(k_fused_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
@@ -369,7 +412,8 @@ cudaError_t tc_launch(sv_state *h, const TcArgs &args, const void *dA) {
     int sms = 0;
     const cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
     if (e != cudaSuccess) return e;
-    const uint64_t grid = a.ntiles < uint64_t(sms) ? a.ntiles : uint64_t(sms);
+    const uint64_t sets = (a.ntiles + kTcGroups - 1) / kTcGroups;  // kTcGroups tiles in flight per CTA
+    const uint64_t grid = sets < uint64_t(sms) ? sets : uint64_t(sms);
     k_fused_tc<<<unsigned(grid), kTcThreads, smem, h->stream>>>(static_cast<float2 *>(h->data),
                                                                 static_cast<const uint4 *>(dA), h->d_err, a);
     return cudaGetLastError();
