@@ -375,6 +375,61 @@ def bench_cut(S, C):
             "mean_abs2_times_2^48": float((abs(amps) ** 2).mean() * 2.0 ** 48)}
 
 
+def bench_qft(S, C, hbm_peak):
+    """QFT-32 of the basis state x = 0x9E3779B9 (32 H + 496 CP + 16 SWAP, 544
+    gates), complex64, tiled and fused modes; sampled amplitudes against the
+    closed form 2^(-16) exp(2 pi i x y / 2^32)."""
+    import numpy as np
+    import torch
+
+    n, x = 32, 0x9E3779B9
+    circ = C.qft_circuit(n, x)
+    st = S.StateVector(n, "c64")
+    out = {"workload": f"QFT-32 of |{x:#x}>, {len(circ)} gates, complex64"}
+    ys = np.array([0, 1, 12345, x, (1 << 32) - 1, 0xDEADBEEF], dtype=np.uint64)
+    for mode in ("tiled", "fused"):
+        plan = st.plan(circ, mode)
+        t, _ = time_plan(S, st, plan, 2, 1, 1)
+        st.set_basis(0)
+        plan.execute()
+        got = st.amplitudes(ys)
+        ref = 2.0 ** -16 * np.exp(2j * np.pi * ((x * ys.astype(object)) % (1 << 32)).astype(np.float64) / 2.0 ** 32)
+        out[mode] = {"gates_per_s": plan.gates * 2 / t, "ms_per_circuit": 1e3 * t / 2, "launches": plan.passes,
+                     "gbs": plan.bytes * 2 / t / 1e9,
+                     "max_abs_err_sampled": float(np.max(np.abs(got - ref))) / 2.0 ** -16}
+        plan.free()
+    st.free()
+    del st
+    torch.cuda.empty_cache()
+    return out
+
+
+def bench_h_sweep(S, C, hbm_peak, peak_kind):
+    """Dense H on every target t = 0..31 of a 32-qubit complex64 state, one
+    per-gate launch each (68.7 GB algorithmic), against the measured HBM copy
+    rate."""
+    import torch
+
+    n = 32
+    st = S.StateVector(n, "c64")
+    rates = []
+    for t in range(n):
+        c = C.Circuit(n)
+        c.add("H", t)
+        plan = st.plan(c, "pergate")
+        _, per_launch = time_plan(S, st, plan, 2, 1, 1)
+        ms = sum(per_launch[k][0] for k in range(2)) / 2
+        rates.append(plan.bytes / (ms / 1e3) / 1e9)
+        plan.free()
+    st.free()
+    del st
+    torch.cuda.empty_cache()
+    srt = sorted(rates)
+    return {"workload": "H on target t = 0..31, 32 qubits complex64, one launch each",
+            "gbs_per_target": [round(r, 1) for r in rates], "min_gbs": srt[0], "median_gbs": srt[len(srt) // 2],
+            "min_frac": srt[0] / hbm_peak, "peak": hbm_peak, "peak_kind": peak_kind}
+
+
 def best_mode(S, state, circ):
     for mode in ("tiled", "fused", "pergate"):
         try:
@@ -514,7 +569,8 @@ def run_ours(args, world, rank, local):
         state.free()
         del state
         torch.cuda.empty_cache()
-        extras = {"enc2b_35q": bench_enc2b(S, C, args, world, hbm_peak, peak_kind), "cut_48q": bench_cut(S, C)}
+        extras = {"enc2b_35q": bench_enc2b(S, C, args, world, hbm_peak, peak_kind), "cut_48q": bench_cut(S, C),
+                  "qft_32q": bench_qft(S, C, hbm_peak), "h_sweep_32q": bench_h_sweep(S, C, hbm_peak, peak_kind)}
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "gates/s", "n_gpus": world, "steps": args.steps,

@@ -1,6 +1,8 @@
 // Plan creation and replay.
 #include <string>
 
+#include <mutex>
+#include <unordered_map>
 #include "plan.h"
 
 namespace sv {
@@ -122,6 +124,31 @@ using namespace sv;
 
 extern "C" {
 
+namespace sv {
+namespace {
+
+// Tiled plans by circuit text: a repeated circuit skips parsing, planning and
+// code generation (its compiled passes stay loaded for the process).  The key
+// holds everything the plan depends on: device, dtype, qubit count, planner
+// and code-generation settings, and the text.
+struct TileCacheEntry {
+    std::vector<void *> fns;
+    int rb = 0;
+    int64_t gates = 0;
+};
+std::mutex g_tile_cache_mu;
+std::unordered_map<std::string, TileCacheEntry> g_tile_cache;
+constexpr size_t kTileCacheMax = 64;
+
+std::string tile_cache_key(const sv_state *h, const char *text) {
+    return std::to_string(h->device) + "|" + std::to_string(int(h->dt)) + "|" + std::to_string(h->n) + "|rb=" +
+           std::to_string(tile_rb64()) + ",low=" + std::to_string(tile_low64()) + ",look=" +
+           std::to_string(plan_lookahead_width()) + "," + tile_codegen_key() + "|" + text;
+}
+
+}  // namespace
+}  // namespace sv
+
 sv_status sv_plan_create(sv_handle h, const char *text, int mode, sv_plan *out) {
     if (!out) {
         set_error("out is NULL");
@@ -140,6 +167,30 @@ sv_status sv_plan_create(sv_handle h, const char *text, int mode, sv_plan *out) 
         set_error("the two-byte code runs one decode-gate-encode pass per gate (SV_MODE_PERGATE)");
         return SV_ERR_DTYPE;
     }
+    const int tile_m = h->dt == SV_C64 ? kTileM64 : kTileM128;
+    const bool tiled = mode == SV_MODE_TILED && h->n >= tile_m;
+    std::string key;
+    if (tiled && text) {
+        key = tile_cache_key(h, text);
+        std::lock_guard<std::mutex> lock(g_tile_cache_mu);
+        auto it = g_tile_cache.find(key);
+        if (it != g_tile_cache.end()) {
+            sv_plan_s *p = new sv_plan_s;
+            p->h = h;
+            p->mode = mode;
+            p->gates = it->second.gates;
+            p->tfns = it->second.fns;
+            p->tile_rb = it->second.rb;
+            const double pass_bytes = 2.0 * double(uint64_t(1) << h->n) * (h->dt == SV_C64 ? 8.0 : 16.0);
+            for (size_t i = 0; i < p->tfns.size(); ++i) {
+                p->launches.push_back(PlanLaunch{1, int(i), pass_bytes});
+                p->bytes += pass_bytes;
+            }
+            h->live_plans++;
+            *out = p;
+            return SV_OK;
+        }
+    }
     Circuit c;
     sv_status s = parse_circuit(text, h->n, &c);
     if (s) return s;
@@ -147,7 +198,6 @@ sv_status sv_plan_create(sv_handle h, const char *text, int mode, sv_plan *out) 
     p->h = h;
     p->mode = mode;
     p->gates = int64_t(c.instrs.size());
-    const int tile_m = h->dt == SV_C64 ? kTileM64 : kTileM128;
     if (mode == SV_MODE_FUSED) {
         s = build_fused_plan(h, c, p);
         if (s) {
@@ -167,6 +217,11 @@ sv_status sv_plan_create(sv_handle h, const char *text, int mode, sv_plan *out) 
         if (s) {
             destroy_plan(p);
             return s;
+        }
+        if (!key.empty()) {
+            std::lock_guard<std::mutex> lock(g_tile_cache_mu);
+            if (g_tile_cache.size() >= kTileCacheMax) g_tile_cache.clear();
+            g_tile_cache[key] = TileCacheEntry{p->tfns, p->tile_rb, p->gates};
         }
     }
     h->live_plans++;

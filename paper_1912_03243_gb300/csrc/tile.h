@@ -17,6 +17,7 @@
 #pragma once
 
 #include <cstdint>
+#include <string>
 #include <vector>
 
 #include "sv_internal.h"
@@ -136,5 +137,10 @@ int tile_low64();
 // 2^(m-rb) threads).
 cudaError_t launch_jit_pass(sv_state *h, void *fn, int n, int rb);
 const char *tile_kernel_name(const sv_state *h);
+// The code-generation switches (environment) that shape a compiled pass, as
+// part of a plan-cache key.
+std::string tile_codegen_key();
+// Planner lookahead width (SV_PLAN_LOOKAHEAD, default 4; 0 = greedy).
+int plan_lookahead_width();
 
 }  // namespace sv

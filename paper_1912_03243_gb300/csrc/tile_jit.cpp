@@ -667,6 +667,10 @@ sv_status compile_check_impl(const TilePlan<R> &tp) {
 
 }  // namespace
 
+std::string tile_codegen_key() {
+    return "f32x2=" + std::to_string(int(packed_adds_enabled())) + ",ctas=" + std::to_string(tile_ctas_per_sm());
+}
+
 sv_status jit_tile_plan(const TilePlan<float> &tp, std::vector<void *> *fns) { return jit_plan_impl(tp, fns); }
 sv_status jit_tile_plan(const TilePlan<double> &tp, std::vector<void *> *fns) { return jit_plan_impl(tp, fns); }
 sv_status jit_compile_check(const TilePlan<float> &tp) { return compile_check_impl(tp); }

@@ -156,3 +156,30 @@ def test_register_budget_variants(S, orc, monkeypatch, ctas):
     s = S.StateVector(21, "c64")
     s.run(c, "tiled")
     check("c64", s.to_numpy(), orc.run(c))
+
+
+def test_plan_cache_reuse(S, orc):
+    """Tiled plans are cached by circuit text (with the device, dtype, qubit
+    count and planner settings in the key): running the same text again on a
+    second state, in complex128, and the same gates on a larger state gives
+    the oracle's state every time; a text for another qubit count is still
+    refused."""
+    c = C.random_circuit(15, 12, 21)
+    text = c.text()
+    ref = orc.run(c)
+    for _ in range(2):
+        s = S.StateVector(15, "c64")
+        s.run(text, "tiled")
+        check("c64", s.to_numpy(), ref)
+    s = S.StateVector(15, "c128")
+    s.run(text, "tiled")
+    check("c128", s.to_numpy(), ref)
+    # the same gates declared for 17 qubits: another text, another plan
+    big = C.Circuit(17)
+    big.gates = list(c.gates)
+    s = S.StateVector(17, "c64")
+    s.run(big.text(), "tiled")
+    check("c64", s.to_numpy(), orc.run(big))
+    # a text declaring 15 qubits is refused on a 17-qubit state, cached or not
+    with pytest.raises(S.SVError):
+        s.run(text, "tiled")
