@@ -12,22 +12,26 @@
 // Al = bf16(A - Ah)); D = Ah Bh + Ah Bl + Al Bh accumulates in FP32 in tensor
 // memory (relative error about 2^-16 per product instead of 2^-8).
 //
-// Per CTA (persistent, one per SM, two groups of 256 threads that share A
-// and otherwise work like separate CTAs: own B, staging tile, TMEM columns,
-// mbarrier and named barrier) and per tile of 2^12 amplitudes (the k block
-// qubits plus the lowest other qubits; B is 128 x 64):
-//   cp.async the tile into the group's staging tile (FP32, swizzled) ->
-//   convert to Bh, Bl in the K-major no-swizzle canonical layout -> one
-//   thread issues 3 x 8 tcgen05.mma (M = 128, N = 64, K = 16 each) into the
-//   group's 64 TMEM columns and commits to its mbarrier -> the group waits
-//   (bounded by %globaltimer) -> each warp reads its 32 TMEM lanes with
-//   tcgen05.ld and scatters FP32 results back to the staging tile ->
-//   coalesced 16-byte stores to HBM.  The groups' phases interleave: some
-//   convert or read back while others wait for memory or for their MMAs.
-// Operand layout (both K-major, no swizzle): element (row, kk) at byte
+// Per CTA (persistent, one per SM, two groups of 256 threads): A lives in
+// tensor memory (row m in lane m, two BF16 K elements per 32-bit column; A_hi
+// in columns 0-63, A_lo in 64-127, written once), which leaves shared memory
+// to the groups: each has its own B operand, two FP32 staging tiles, 64 TMEM
+// accumulator columns, mbarrier and named barrier.  Per tile of 2^12
+// amplitudes (the k block qubits plus the lowest other qubits; B is 128 x 64)
+// and group:
+//   the tile's cp.async was issued one tile earlier into one staging tile,
+//   the next tile's goes into the other now -> convert to Bh, Bl in the
+//   K-major no-swizzle canonical layout -> one thread issues 3 x 8
+//   tcgen05.mma (A from tensor memory, M = 128, N = 64, K = 16 each) and
+//   commits to the group's mbarrier -> the group waits (bounded by
+//   %globaltimer) -> each warp reads its 32 TMEM lanes with tcgen05.ld and
+//   scatters FP32 results back to the staging tile -> coalesced 16-byte
+//   stores to HBM.
+// B operand layout (K-major, no swizzle): element (row, kk) at byte
 // (row%8)*16 + (kk%8)*2 + (kk/8)*128 + (row/8)*2048; leading-dimension byte
 // offset 128 (next 8 K-elements), stride-dimension byte offset 2048 (next 8
-// rows); the K-slice s of an instruction starts at + 256 s.
+// rows); the K-slice s of an instruction starts at + 256 s (and at column
+// + 8 s of A in tensor memory).
 #include <cuda_bf16.h>
 
 #include <cstring>
@@ -42,8 +46,10 @@ namespace {
 constexpr int kTcGroup = 256;                  // threads of one group
 constexpr int kTcGroups = 2;                   // groups (tiles in flight) per CTA
 constexpr int kTcThreads = kTcGroups * kTcGroup;
-constexpr int kTcCols = kTcGroups * kTcN;      // TMEM columns: one N-column accumulator per group
-constexpr uint32_t kOpBytes = 128 * 128 * 2;   // one BF16 A operand (32 KiB)
+constexpr int kTcACols = 64;                   // TMEM columns of one 128 x 128 BF16 A operand
+constexpr int kTcCols = 2 * kTcACols + kTcGroups * kTcN;  // A_hi, A_lo, one accumulator per group (256)
+static_assert(kTcCols == 256, "tensor memory allocation is a power of two");
+constexpr uint32_t kOpBytes = 128 * 128 * 2;   // one BF16 A operand image (32 KiB)
 constexpr uint32_t kBBytes = kTcN * 128 * 2;   // one BF16 B operand (16 KiB)
 constexpr uint32_t kStageBytes = (1u << kTcM) * 8;  // one FP32 staging tile (32 KiB)
 constexpr int kChunkIters = (1 << kTcM) / 2 / kTcGroup;  // 16-byte chunks per thread and tile
@@ -87,12 +93,30 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t
 // bits 24-28 (M = 128, N = kTcN).
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t(kTcN) >> 3) << 17) | ((128u >> 4) << 24);
 
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accum) {
+// D (tensor memory) [+]= A (tensor memory) x B (shared memory descriptor)
+__device__ __forceinline__ void mma_bf16_ts(uint32_t tmem_d, uint32_t tmem_a, uint64_t bdesc, uint32_t accum) {
     asm volatile(
         "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
-        "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accum)
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "r"(tmem_a), "l"(bdesc), "r"(kIdesc), "r"(accum)
         : "memory");
+}
+
+// 64 consecutive 32-bit columns of this warp's 32 lanes <- r
+__device__ __forceinline__ void tmem_st64(uint32_t taddr, const uint32_t *r) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x64.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+        "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,"
+        "%43,%44,%45,%46,%47,%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63,%64};\n" ::"r"(taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
+        "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]), "r"(r[17]), "r"(r[18]),
+        "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]),
+        "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31]), "r"(r[32]), "r"(r[33]), "r"(r[34]), "r"(r[35]), "r"(r[36]),
+        "r"(r[37]), "r"(r[38]), "r"(r[39]), "r"(r[40]), "r"(r[41]), "r"(r[42]), "r"(r[43]), "r"(r[44]), "r"(r[45]),
+        "r"(r[46]), "r"(r[47]), "r"(r[48]), "r"(r[49]), "r"(r[50]), "r"(r[51]), "r"(r[52]), "r"(r[53]), "r"(r[54]),
+        "r"(r[55]), "r"(r[56]), "r"(r[57]), "r"(r[58]), "r"(r[59]), "r"(r[60]), "r"(r[61]), "r"(r[62]), "r"(r[63])
+        : "memory");
+    asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
 }
 
 // kTcN / 2 consecutive columns of this warp's 32 lanes
@@ -135,10 +159,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fused_tc(float2 *__restrict__
     __shared__ uint16_t sHi[kChunkIters];                  // swizzled chunk of the chunk bits above 7
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int g = tid / kTcGroup, lt = tid % kTcGroup, gw = warp & 7;  // group, thread and warp in the group
-    unsigned char *sAh = smem, *sAl = smem + kOpBytes;
-    unsigned char *gbase = smem + 2 * kOpBytes + size_t(g) * (2 * kBBytes + kStageBytes);
+    unsigned char *gbase = smem + size_t(g) * (2 * kBBytes + 2 * kStageBytes);
     unsigned char *sBh = gbase, *sBl = gbase + kBBytes;
-    float2 *sX = reinterpret_cast<float2 *>(gbase + 2 * kBBytes);  // 2^kTcM amplitudes
+    unsigned char *sStage = gbase + 2 * kBBytes;  // two FP32 staging tiles of 2^kTcM amplitudes
     const uint32_t mbar_a = smem_u32(&mbar[g]);
 
     for (int i = tid; i < 64; i += kTcThreads) {
@@ -184,13 +207,30 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fused_tc(float2 *__restrict__
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
     }
-    // the A operands (Ah then Al, 64 KiB) are the same for every tile
-    for (int i = tid; i < int(2 * kOpBytes / 16); i += kTcThreads) cp_async16(smem_u32(smem + 16 * i), gA + i);
-    cp_async_wait_all();
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();  // tmem_slot
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    // the A operands go to tensor memory once: group 0's warp w writes lanes
+    // 32 (w % 4) .. +31 of A_hi (w < 4) or A_lo (w >= 4), one row per thread
+    // (gA: row-major BF16, A_hi then A_lo)
+    if (g == 0) {
+        const int q = gw & 3, h = gw >> 2, m = 32 * q + lane;
+        uint32_t r[64];
+        const uint4 *src = gA + (size_t(h) * 128 * 128 * 2 + size_t(m) * 256) / 16;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const uint4 v = src[i];
+            r[4 * i] = v.x;
+            r[4 * i + 1] = v.y;
+            r[4 * i + 2] = v.z;
+            r[4 * i + 3] = v.w;
+        }
+        tmem_st64(tmem_slot + (uint32_t(32 * q) << 16) + uint32_t(kTcACols * h), r);
+    }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-    const uint32_t tmem = tmem_slot + uint32_t(g * kTcN);  // this group's accumulator columns
+    const uint32_t tmem = tmem_slot + uint32_t(2 * kTcACols + g * kTcN);  // this group's accumulator columns
     const int klog = a.k + 1, rmask = (2 << a.k) - 1;        // 2d = 2^(k+1)
     // K element kk = 2i, 2i + 1 (re, im of one amplitude): pack p = kk >> klog,
     // real row r = kk & rmask (tables written before the barrier above)
@@ -200,18 +240,35 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fused_tc(float2 *__restrict__
     const uint32_t srow = tL[(drow & rmask) >> 1] ^ tP[drow >> klog];
     const int dcomp = drow & 1;
 
-    uint32_t phase = 0;
-    const uint64_t stride = uint64_t(kTcGroups) * gridDim.x;
-    for (uint64_t tile = uint64_t(kTcGroups) * blockIdx.x + uint64_t(g); tile < a.ntiles; tile += stride) {
-        const uint64_t base = tB[0][tile & 255] | tB[1][(tile >> 8) & 255] | tB[2][(tile >> 16) & 255] |
-                              tB[3][(tile >> 24) & 255];
-        // load: 16-byte chunks c = lt + 256 i (2 amplitudes, tile index 2c);
-        // offsets split into a per-thread and a per-i part (disjoint bits)
+    auto tile_base = [&](uint64_t tile) {
+        return tB[0][tile & 255] | tB[1][(tile >> 8) & 255] | tB[2][(tile >> 16) & 255] | tB[3][(tile >> 24) & 255];
+    };
+    // 16-byte chunks c = lt + 256 i (2 amplitudes, tile index 2c); offsets
+    // split into a per-thread and a per-i part (disjoint bits)
+    auto load_tile = [&](uint64_t tile, int buf) {
+        const uint64_t base = tile_base(tile);
+        float2 *sx = reinterpret_cast<float2 *>(sStage + buf * kStageBytes);
 #pragma unroll
         for (int i = 0; i < kChunkIters; ++i)
-            cp_async16(smem_u32(sX + 2 * (sLo ^ sHi[i])), psi + (base | gLo | gHi[i]));
-        cp_async_wait_all();
+            cp_async16(smem_u32(sx + 2 * (sLo ^ sHi[i])), psi + (base | gLo | gHi[i]));
+    };
+
+    uint32_t phase = 0;
+    int buf = 0;
+    const uint64_t stride = uint64_t(kTcGroups) * gridDim.x;
+    const uint64_t first = uint64_t(kTcGroups) * blockIdx.x + uint64_t(g);
+    // one cp.async group per tile: wait_group 1 leaves only the newest (the
+    // next tile's) in flight
+    if (first < a.ntiles) load_tile(first, 0);
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    for (uint64_t tile = first; tile < a.ntiles; tile += stride, buf ^= 1) {
+        // the other staging tile was stored before the last iteration's
+        // closing barrier
+        if (tile + stride < a.ntiles) load_tile(tile + stride, buf ^ 1);
+        asm volatile("cp.async.commit_group;\ncp.async.wait_group 1;\n" ::: "memory");
         group_sync(g);
+        float2 *sX = reinterpret_cast<float2 *>(sStage + buf * kStageBytes);
+        const uint64_t base = tile_base(tile);
         // convert: one task = one B row n and 8 consecutive K elements (16 B
         // of Bh and of Bl); a thread's row n = lt % kTcN is the same in all
         // its tasks
@@ -238,14 +295,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fused_tc(float2 *__restrict__
         group_sync(g);
         if (lt == 0 && !a.skip_mma) {
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-            const uint32_t ah = smem_u32(sAh), al = smem_u32(sAl), bh = smem_u32(sBh), bl = smem_u32(sBl);
+            const uint32_t bh = smem_u32(sBh), bl = smem_u32(sBl);
             uint32_t acc = 0;
 #pragma unroll
             for (int pass = 0; pass < 3; ++pass) {
-                const uint32_t aa = pass == 2 ? al : ah, bb = pass == 1 ? bl : bh;
+                const uint32_t aa = tmem_slot + uint32_t(pass == 2 ? kTcACols : 0), bb = pass == 1 ? bl : bh;
 #pragma unroll
                 for (int s = 0; s < 8; ++s) {
-                    mma_bf16(tmem, sdesc(aa + 256u * s, 128, 2048), sdesc(bb + 256u * s, 128, 2048), acc);
+                    mma_bf16_ts(tmem, aa + 8u * s, sdesc(bb + 256u * s, 128, 2048), acc);
                     acc = 1;
                 }
             }
@@ -292,6 +349,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fused_tc(float2 *__restrict__
                 *reinterpret_cast<const float4 *>(sX + 2 * (sLo ^ sHi[i]));
         group_sync(g);
     }
+    // no copy may still be writing shared memory when the CTA leaves
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
     if (abort_flag[g] && lt == 0) atomicExch(err, int(SV_ERR_TIMEOUT));
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
@@ -322,7 +381,7 @@ bool fused_tc_supported(const sv_state *h) { return h->dt == SV_C64 && h->n >= k
 
 void tc_prepare(int n, int k, const int *qubits, const double *U, uint16_t *a_ops, TcArgs *args) {
     const int d = 1 << k, twoD = 2 * d, P = 64 / d;
-    // A = I_P (x) Ut, split into BF16 hi / lo, K-major no-swizzle layout
+    // A = I_P (x) Ut, split into BF16 hi / lo, row-major (one row per tensor-memory lane)
     for (int i = 0; i < 2 * 128 * 128; ++i) a_ops[i] = 0;
     for (int m = 0; m < 128; ++m)
         for (int kk = 0; kk < 128; ++kk) {
@@ -334,7 +393,7 @@ void tc_prepare(int n, int k, const int *qubits, const double *U, uint16_t *a_op
             }
             const uint16_t hi = bf16_rne_host(float(v));
             const uint16_t lo = bf16_rne_host(float(v - double(bf16_to_float_host(hi))));
-            const size_t off = size_t((m % 8) * 8 + (kk % 8) + (kk / 8) * 64 + (m / 8) * 1024);  // in elements
+            const size_t off = size_t(m) * 128 + size_t(kk);  // row-major (tensor-memory rows)
             a_ops[off] = hi;
             a_ops[128 * 128 + off] = lo;
         }
@@ -402,7 +461,7 @@ cudaError_t tc_launch(sv_state *h, const TcArgs &args, const void *dA) {
         const cudaError_t e = ensure_err_word(h);
         if (e != cudaSuccess) return e;
     }
-    const size_t smem = 2 * size_t(kOpBytes) + kTcGroups * (2 * size_t(kBBytes) + size_t(kStageBytes));
+    const size_t smem = kTcGroups * (2 * size_t(kBBytes) + 2 * size_t(kStageBytes));
     static bool configured = false;
     if (!configured) {
         const cudaError_t e = cudaFuncSetAttribute(k_fused_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
