@@ -430,6 +430,28 @@ def bench_h_sweep(S, C, hbm_peak, peak_kind):
             "min_frac": srt[0] / hbm_peak, "peak": hbm_peak, "peak_kind": peak_kind}
 
 
+def bench_30q(S, C, hbm_peak):
+    """The 30-qubit depth-16 random circuit (712 gates) in tiled mode, complex64
+    (8 GiB) and complex128 (16 GiB; its passes are bound by GB300's FP64 rate)."""
+    import torch
+
+    n, depth = 30, 16
+    circ = C.random_circuit(n, depth, 1)
+    out = {"workload": f"random circuit, {n} qubits, depth {depth}, seed 1 ({len(circ)} gates), tiled"}
+    for dt, steps in (("c64", 3), ("c128", 1)):
+        st = S.StateVector(n, dt)
+        plan = st.plan(circ, "tiled")
+        t, _ = time_plan(S, st, plan, steps, 1, 1)
+        gbs = plan.bytes * steps / t / 1e9
+        out[dt] = {"gates_per_s": plan.gates * steps / t, "ms_per_circuit": 1e3 * t / steps, "launches": plan.passes,
+                   "gbs": gbs, "frac_of_measured_hbm": gbs / hbm_peak}
+        plan.free()
+        st.free()
+        del st
+        torch.cuda.empty_cache()
+    return out
+
+
 def best_mode(S, state, circ):
     for mode in ("tiled", "fused", "pergate"):
         try:
@@ -570,7 +592,8 @@ def run_ours(args, world, rank, local):
         del state
         torch.cuda.empty_cache()
         extras = {"enc2b_35q": bench_enc2b(S, C, args, world, hbm_peak, peak_kind), "cut_48q": bench_cut(S, C),
-                  "qft_32q": bench_qft(S, C, hbm_peak), "h_sweep_32q": bench_h_sweep(S, C, hbm_peak, peak_kind)}
+                  "qft_32q": bench_qft(S, C, hbm_peak), "h_sweep_32q": bench_h_sweep(S, C, hbm_peak, peak_kind),
+                  "random_30q": bench_30q(S, C, hbm_peak)}
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "gates/s", "n_gpus": world, "steps": args.steps,

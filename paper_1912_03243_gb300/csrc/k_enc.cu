@@ -75,6 +75,40 @@ __device__ __forceinline__ void gate_pair(const float *u, float &ar, float &ai, 
     bi = i1;
 }
 
+// Shape of the 2x2 matrix, chosen on the host from exact zeros: the general
+// fixed-order update above, or the same update with the terms of zero
+// coefficients left out.  A left-out term contributes fmaf(0, x, y) = y up to
+// the sign of a zero, and a zero (of either sign) encodes to code 0 and does
+// not change a block maximum, so the codes are those of the general form.
+enum EncShape { ENC_GENERAL = 0, ENC_REAL = 1, ENC_DIAG = 2, ENC_DIAG1 = 3 };
+
+template <int SHAPE>
+__device__ __forceinline__ void gate_pair_s(const float *u, float &ar, float &ai, float &br, float &bi) {
+    if constexpr (SHAPE == ENC_REAL) {  // every imaginary part 0 (u[1] = u[3] = u[5] = u[7] = 0)
+        const float r0 = __fmaf_rn(u[0], ar, __fmul_rn(u[2], br));
+        const float i0 = __fmaf_rn(u[0], ai, __fmul_rn(u[2], bi));
+        const float r1 = __fmaf_rn(u[4], ar, __fmul_rn(u[6], br));
+        const float i1 = __fmaf_rn(u[4], ai, __fmul_rn(u[6], bi));
+        ar = r0;
+        ai = i0;
+        br = r1;
+        bi = i1;
+    } else if constexpr (SHAPE == ENC_DIAG || SHAPE == ENC_DIAG1) {  // u01 = u10 = 0
+        if constexpr (SHAPE == ENC_DIAG) {  // (u00 = 1: a unchanged)
+            const float r0 = __fmaf_rn(u[0], ar, -__fmul_rn(u[1], ai));
+            const float i0 = __fmaf_rn(u[0], ai, __fmul_rn(u[1], ar));
+            ar = r0;
+            ai = i0;
+        }
+        const float r1 = __fmaf_rn(u[6], br, -__fmul_rn(u[7], bi));
+        const float i1 = __fmaf_rn(u[6], bi, __fmul_rn(u[7], br));
+        br = r1;
+        bi = i1;
+    } else {
+        gate_pair(u, ar, ai, br, bi);
+    }
+}
+
 __device__ __forceinline__ float warp_max(float v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
@@ -125,6 +159,7 @@ __device__ __forceinline__ bool ctl_ok(int c, int lane, int j) {
 }
 
 // Target inside the block (t < 8).
+template <int SHAPE>
 __global__ void __launch_bounds__(32 * kWarpsPerCta) k_enc_gate_in(int4 *__restrict__ codes, float *__restrict__ scales,
                                                                    EncGateArgs a) {
     __shared__ float tab[kTabFloats];
@@ -146,7 +181,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta) k_enc_gate_in(int4 *__restr
             for (int j = 0; j < 8; ++j) {
                 if (j & tb) continue;
                 if (!ctl_ok(a.c, lane, j)) continue;
-                gate_pair(a.u, x.re[j], x.im[j], x.re[j | tb], x.im[j | tb]);
+                gate_pair_s<SHAPE>(a.u, x.re[j], x.im[j], x.re[j | tb], x.im[j | tb]);
             }
         } else {
             const int lb = 1 << (a.t - 3);
@@ -158,7 +193,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta) k_enc_gate_in(int4 *__restr
                 if (!ctl_ok(a.c, lane, j)) continue;
                 float ar = upper ? pr : x.re[j], ai = upper ? pi : x.im[j];
                 float br = upper ? x.re[j] : pr, bi = upper ? x.im[j] : pi;
-                gate_pair(a.u, ar, ai, br, bi);
+                gate_pair_s<SHAPE>(a.u, ar, ai, br, bi);
                 x.re[j] = upper ? br : ar;
                 x.im[j] = upper ? bi : ai;
             }
@@ -170,6 +205,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta) k_enc_gate_in(int4 *__restr
 }
 
 // Target across blocks (t >= 8): the warp holds block b0 and b0 + 2^(t-8).
+template <int SHAPE>
 __global__ void __launch_bounds__(32 * kWarpsPerCta) k_enc_gate_across(int4 *__restrict__ codes,
                                                                        float *__restrict__ scales, EncGateArgs a) {
     __shared__ float tab[kTabFloats];
@@ -190,7 +226,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta) k_enc_gate_across(int4 *__r
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             if (!ctl_ok(a.c, lane, j)) continue;
-            gate_pair(a.u, x.re[j], x.im[j], y.re[j], y.im[j]);
+            gate_pair_s<SHAPE>(a.u, x.re[j], x.im[j], y.re[j], y.im[j]);
         }
         const float n0 = warp_max(lane_absmax(x));
         const float n1 = warp_max(lane_absmax(y));
@@ -476,10 +512,27 @@ cudaError_t launch_enc_gate1(sv_state *h, const Gate1 &g) {
         k_enc_xblocks<<<enc_grid(a.nwork), 256, 0, h->stream>>>(reinterpret_cast<uint4 *>(codes), h->scales, a);
         return cudaGetLastError();
     }
-    if (a.t < kEncBlockLog2)
-        k_enc_gate_in<<<enc_grid(a.nwork), 32 * kWarpsPerCta, 0, h->stream>>>(codes, h->scales, a);
-    else
-        k_enc_gate_across<<<enc_grid(a.nwork), 32 * kWarpsPerCta, 0, h->stream>>>(codes, h->scales, a);
+    // matrix shape from exact zeros of the FP32 entries the kernel uses
+    const bool real = a.u[1] == 0.0f && a.u[3] == 0.0f && a.u[5] == 0.0f && a.u[7] == 0.0f;
+    const bool diag = a.u[2] == 0.0f && a.u[3] == 0.0f && a.u[4] == 0.0f && a.u[5] == 0.0f;
+    const bool one = diag && a.u[0] == 1.0f && a.u[1] == 0.0f;
+    const int shape = one ? ENC_DIAG1 : diag ? ENC_DIAG : real ? ENC_REAL : ENC_GENERAL;
+    const unsigned grid = enc_grid(a.nwork), block = 32 * kWarpsPerCta;
+    if (a.t < kEncBlockLog2) {
+        switch (shape) {
+            case ENC_REAL: k_enc_gate_in<ENC_REAL><<<grid, block, 0, h->stream>>>(codes, h->scales, a); break;
+            case ENC_DIAG: k_enc_gate_in<ENC_DIAG><<<grid, block, 0, h->stream>>>(codes, h->scales, a); break;
+            case ENC_DIAG1: k_enc_gate_in<ENC_DIAG1><<<grid, block, 0, h->stream>>>(codes, h->scales, a); break;
+            default: k_enc_gate_in<ENC_GENERAL><<<grid, block, 0, h->stream>>>(codes, h->scales, a); break;
+        }
+    } else {
+        switch (shape) {
+            case ENC_REAL: k_enc_gate_across<ENC_REAL><<<grid, block, 0, h->stream>>>(codes, h->scales, a); break;
+            case ENC_DIAG: k_enc_gate_across<ENC_DIAG><<<grid, block, 0, h->stream>>>(codes, h->scales, a); break;
+            case ENC_DIAG1: k_enc_gate_across<ENC_DIAG1><<<grid, block, 0, h->stream>>>(codes, h->scales, a); break;
+            default: k_enc_gate_across<ENC_GENERAL><<<grid, block, 0, h->stream>>>(codes, h->scales, a); break;
+        }
+    }
     return cudaGetLastError();
 }
 
