@@ -191,6 +191,20 @@ sv_status sv_amplitudes(sv_handle h, size_t m, const uint64_t *idx, double *out)
  * precision, FP64 beyond), deterministic.  Synchronises. */
 sv_status sv_norm(sv_handle h, double *out);
 
+/* Expectation values <psi| sigma^alpha_i |psi> for every qubit i and
+ * alpha = x, y, z (Sec. 3: the validation observable is
+ * <Q_alpha(i)> = (1 - <sigma^alpha_i>)/2 of the normalised state).
+ * out: caller-owned host array of 3n doubles, out[3 i + alpha] with
+ * alpha 0 = x, 1 = y, 2 = z; not divided by the norm.  Works on SV_C64,
+ * SV_C128 and SV_ENC2B (decoded on the fly, codes untouched).  Read-only
+ * passes over the state in tiles of 2^13 amplitudes (2^12 for SV_C128) that
+ * keep the low qubits (4; the 8 in-block ones for SV_ENC2B): 1 +
+ * ceil((n - 13) / 9) passes for SV_C64.  Per-tile sums in the storage
+ * precision, FP64 across tiles.  Synchronises.  Errors: SV_ERR_ARG (NULL),
+ * SV_ERR_UNSUPPORTED (more than 40 qubits outside one tile), SV_ERR_OOM or
+ * SV_ERR_CUDA (a small partial-sum buffer is allocated per call). */
+sv_status sv_expect_pauli(sv_handle h, double *out);
+
 /* Raw copy of the whole state between device and host memory (bytes must be
  * sv_bytes_required).  Synchronises. */
 sv_status sv_copy_to_host(sv_handle h, void *dst, size_t bytes);

@@ -58,6 +58,7 @@ SIGNATURES = {
     "sv_get_codes": (_st, [_vp, ctypes.POINTER(ctypes.c_int8), ctypes.POINTER(ctypes.c_float)]),
     "sv_amplitudes": (_st, [_vp, ctypes.c_size_t, _u64p, _dp]),
     "sv_norm": (_st, [_vp, _dp]),
+    "sv_expect_pauli": (_st, [_vp, _dp]),
     "sv_amplitudes_noalloc": (_st, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_size_t, _u64p, _dp, _vp]),
     "sv_copy_to_host": (_st, [_vp, _vp, ctypes.c_size_t]),
     "sv_copy_from_host": (_st, [_vp, _vp, ctypes.c_size_t]),
@@ -299,6 +300,13 @@ class StateVector:
         out = ctypes.c_double()
         _check(lib().sv_norm(self.handle, ctypes.byref(out)), "sv_norm")
         return out.value
+
+    def expect_pauli(self) -> np.ndarray:
+        """<sigma^alpha_i> for every qubit: an (n, 3) array, columns x, y, z
+        (not divided by the norm)."""
+        out = np.zeros(3 * self.n, dtype=np.float64)
+        _check(lib().sv_expect_pauli(self.handle, _dptr(out)), "sv_expect_pauli")
+        return out.reshape(self.n, 3)
 
     def to_numpy(self) -> np.ndarray:
         """Whole state to host (complex64/complex128; raw bytes for enc2b)."""
