@@ -363,15 +363,21 @@ def bench_cut(S, C):
     c = C.grid_circuit(6, 8, 8, 1)
     mask = C.grid_partition_mask(6, 8, 3)
     z = C.random_bitstrings(1024, 48, 7)
-    S.sv_cut_amplitudes(c, 48, mask, z)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    amps, s = S.sv_cut_amplitudes(c, 48, mask, z)
-    torch.cuda.synchronize()
-    t = time.perf_counter() - t0
+    times = {}
+    for label, flag in (("batched", "0"), ("prefix", "1")):
+        os.environ["SV_CUT_PREFIX"] = flag
+        S.sv_cut_amplitudes(c, 48, mask, z)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        amps, s = S.sv_cut_amplitudes(c, 48, mask, z)
+        torch.cuda.synchronize()
+        times[label] = time.perf_counter() - t0
+    os.environ.pop("SV_CUT_PREFIX", None)
     return {"workload": "6x8 grid, 48 qubits, depth 8, rows 0-2 | 3-5, projector decomposition", "cut_gates": s,
-            "branches": 1 << s, "amplitudes": int(z.size), "ms_per_call": 1e3 * t,
-            "note": "end to end: planning, allocation, both batched halves, FP64 branch sum, copy back",
+            "branches": 1 << s, "amplitudes": int(z.size), "ms_per_call": 1e3 * times["prefix"],
+            "ms_per_call_batched": 1e3 * times["batched"],
+            "note": "end to end: planning, allocation, both halves (branch-prefix sharing; batched: every branch "
+                    "from the first gate), FP64 branch sum, copy back",
             "mean_abs2_times_2^48": float((abs(amps) ** 2).mean() * 2.0 ** 48)}
 
 

@@ -17,11 +17,14 @@
 // and D_s are phases selected by (bit, s_k)).  Branch bits only ever appear
 // in diagonal gates, so the tile planner keeps them outside the tiles (a
 // constant per CTA) and every pass runs over all branches of a half in one
-// launch.  The initial vector has amplitude 1 at index s << n_p for every s.
+// launch.  The initial vector has amplitude 1 at index s << n_p for every s
+// (or, with branch-prefix sharing, the branches are forked from branch 0 at
+// their first operator, see run_half).
 //
 // Sum (GPU): one warp per output bit string, lanes over s, products and sum
 // in FP64, times the weight.
 #include <complex>
+#include <cstdlib>
 #include <vector>
 
 #include "plan.h"
@@ -99,27 +102,78 @@ struct Half {
     float2 *d = nullptr;
 };
 
-sv_status run_half(Half &h, cudaStream_t st, int S, std::vector<void *> *fns, TilePlan<float> *tp) {
-    sv_status s = plan_tiles<float>(h.gates, h.nq, TileConfig{kTileM64, tile_rb64(), tile_low64(), true}, tp);
+// Compile and run `gates` as tiled passes over the low 2^nrun amplitudes.
+sv_status run_stage(Half &h, cudaStream_t st, const std::vector<PGate> &gates, int nrun) {
+    if (gates.empty()) return SV_OK;
+    TilePlan<float> tp;
+    sv_status s = plan_tiles<float>(gates, nrun, TileConfig{kTileM64, tile_rb64(), tile_low64(), true}, &tp);
     if (s) return s;
-    s = jit_tile_plan(*tp, fns);
+    std::vector<void *> fns;
+    s = jit_tile_plan(tp, &fns);
     if (s) return s;
     sv_state tmp;
-    tmp.n = h.nq;
+    tmp.n = nrun;
     tmp.dt = SV_C64;
     tmp.data = h.d;
     tmp.stream = st;
     SV_CUDA_TRY(cudaGetDevice(&tmp.device));
-    SV_CUDA_TRY(cudaMemsetAsync(h.d, 0, sizeof(float2) << h.nq, st));
-    k_branch_init<<<64, 256, 0, st>>>(h.d, h.nlocal, S);
-    s = check_launch(cudaGetLastError(), "k_branch_init");
-    if (s) return s;
-    for (void *fn : *fns) {
-        s = check_launch(launch_jit_pass(&tmp, fn, h.nq, tp->rb), "branch pass");
-        if (s) return s;
+    for (void *fn : fns) {
+        s = check_launch(launch_jit_pass(&tmp, fn, nrun, tp.rb), "branch pass");
+        if (s) break;
     }
     tmp.data = nullptr;
-    return SV_OK;
+    return s;
+}
+
+// Branch-prefix sharing (on unless SV_CUT_PREFIX=0): the gates before the
+// first branch operator are the same for every branch, so they run once on
+// the 2^n_p amplitudes of branch 0; at the first operator on branch bit k the
+// live vector (branches with bits >= k clear, the low 2^(n_p + k) amplitudes)
+// is copied to the slots with bit k set, and the following gates run on the
+// doubled vector.  Work falls from 2^S G to the sum over stages of
+// 2^(n_p + k) G_k.  Amplitudes above the live vector are zero until copied
+// to, and gates keep zeros zero, so a stage may run on more qubits (the tile
+// size) than it has live.
+bool prefix_sharing() {
+    const char *e = std::getenv("SV_CUT_PREFIX");
+    return !(e && e[0] == '0');
+}
+
+sv_status run_half(Half &h, cudaStream_t st, int S) {
+    SV_CUDA_TRY(cudaMemsetAsync(h.d, 0, sizeof(float2) << h.nq, st));
+    if (!prefix_sharing()) {
+        k_branch_init<<<64, 256, 0, st>>>(h.d, h.nlocal, S);
+        sv_status s = check_launch(cudaGetLastError(), "k_branch_init");
+        return s ? s : run_stage(h, st, h.gates, h.nq);
+    }
+    k_branch_init<<<1, 32, 0, st>>>(h.d, h.nlocal, 0);
+    sv_status s = check_launch(cudaGetLastError(), "k_branch_init");
+    if (s) return s;
+    int live = h.nlocal;  // live amplitudes: 2^live
+    std::vector<PGate> stage;
+    auto fork = [&]() -> sv_status {
+        s = run_stage(h, st, stage, live > kTileM64 ? live : kTileM64);
+        stage.clear();
+        if (s) return s;
+        const size_t bytes = sizeof(float2) << live;
+        SV_CUDA_TRY(cudaMemcpyAsync(reinterpret_cast<char *>(h.d) + bytes, h.d, bytes, cudaMemcpyDeviceToDevice, st));
+        ++live;
+        return SV_OK;
+    };
+    for (const PGate &g : h.gates) {
+        // branch bits are only ever conditions of diagonal gates
+        const uint64_t branch = g.kind == 1 ? (g.cmask >> h.nlocal) : 0;
+        while (branch >> (live - h.nlocal)) {
+            s = fork();
+            if (s) return s;
+        }
+        stage.push_back(g);
+    }
+    while (live < h.nlocal + S) {  // every branch bit has operators; kept for the layout
+        s = fork();
+        if (s) return s;
+    }
+    return run_stage(h, st, stage, h.nq);
 }
 
 }  // namespace
@@ -280,11 +334,7 @@ static sv_status cut_impl(const char *text, int n, uint64_t maskA, int form, uin
         release();
         return cuda_status(e, "cudaMalloc (decomposition)");
     }
-    for (int p = 0; p < 2 && s == SV_OK; ++p) {
-        std::vector<void *> fns;
-        TilePlan<float> tp;
-        s = run_half(half[p], st, Svar, &fns, &tp);
-    }
+    for (int p = 0; p < 2 && s == SV_OK; ++p) s = run_half(half[p], st, Svar);
     if (s == SV_OK) {
         e = cudaMemcpyAsync(dz, zs.data(), bytesZ, cudaMemcpyHostToDevice, st);
         if (e != cudaSuccess) s = cuda_status(e, "cudaMemcpyAsync");

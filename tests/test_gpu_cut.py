@@ -157,3 +157,20 @@ def test_parts_add_up(S, orc, form):
     assert np.all(far == 0)
     with pytest.raises(S.SVError):
         S.sv_cut_amplitudes_part(c, c.n, mask, z, 4, 2, form=form)
+
+
+@pytest.mark.parametrize("form", [0, 1])
+def test_prefix_sharing_matches_batched(S, monkeypatch, form):
+    """Branch-prefix sharing (branches forked from branch 0 at their first
+    operator) and the fully batched simulation (every branch from the start,
+    SV_CUT_PREFIX=0) give the same amplitudes: the 6x4 check grid, all 2^24
+    outputs, and a grid whose first gates are cut (fork before any gate)."""
+    for c, mask in ((C.grid_circuit(6, 4, 12, 1), C.grid_partition_mask(6, 4, 3)),
+                    (C.grid_circuit(4, 3, 8, 6), C.grid_partition_mask(4, 3, 2))):
+        z = np.arange(1 << min(c.n, 24), dtype=np.uint64)
+        monkeypatch.setenv("SV_CUT_PREFIX", "0")
+        ref, s0 = S.sv_cut_amplitudes(c, c.n, mask, z, form=form)
+        monkeypatch.setenv("SV_CUT_PREFIX", "1")
+        got, s1 = S.sv_cut_amplitudes(c, c.n, mask, z, form=form)
+        assert s0 == s1
+        close(got, ref)
