@@ -487,6 +487,50 @@ def bench_expect(S, C, hbm_peak):
             "note": "host wall time of the synchronous call (passes, partial-sum copies and host sums)"}
 
 
+def bench_ghz_sweep(S, C):
+    """The circuit of the paper's weak-scaling figures (Sec. 3, Figs. 1-2): H on
+    qubit 0, CNOT(i, i+1) for i = 0..n-2, then <sigma^alpha_i> of every qubit;
+    elapsed time per gate operation against n on one GPU, normalised like the
+    figures by the value at n = 32 (complex64) and n = 35 (two-byte code)."""
+    import torch
+
+    out = {"workload": "H(0) + CNOT chain + all expectation values, per-gate mode, one GPU"}
+    for dt, ns, nref in (("c64", range(20, 35, 2), 32), ("enc2b", list(range(21, 36, 2)) + [36], 35)):
+        rows = {}
+        for n in ns:
+            if torch.cuda.mem_get_info()[0] < S.sv_bytes_required(n, dt) + (8 << 30):
+                continue
+            st = S.StateVector(n, dt)
+            circ = C.ghz_circuit(n)
+            plan = st.plan(circ, "pergate")
+            st.set_basis(0)
+            plan.execute()
+            st.expect_pauli()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st.set_basis(0)
+            plan.execute()
+            sig = st.expect_pauli()
+            torch.cuda.synchronize()
+            t = time.perf_counter() - t0
+            rows[n] = {"s_per_gate": t / plan.gates, "gates": plan.gates,
+                       "z0": float(sig[0, 2] / max(st.norm(), 1e-300))}
+            plan.free()
+            st.free()
+            del st
+            torch.cuda.empty_cache()
+        ref = rows.get(nref, {}).get("s_per_gate")
+        for n, r in rows.items():
+            # the figures' form (time per gate / time at the reference n), and
+            # the one-GPU analogue of weak scaling: per amplitude
+            r["normalised"] = r["s_per_gate"] / ref if ref else None
+            r["normalised_per_amplitude"] = r["s_per_gate"] * 2.0 ** (nref - n) / ref if ref else None
+        out[dt] = {"reference_n": nref, "by_n": rows}
+    out["paper_reference"] = ("elapsed s per gate at the normalisation point: JUQCS-E N=32 0.9 (JUWELS) ... 5.1 "
+                              "(Sunway); JUQCS-A N=35 2.2 (JUWELS) ... 19.9 (Sunway); other hardware, context only")
+    return out
+
+
 def best_mode(S, state, circ):
     for mode in ("tiled", "fused", "pergate"):
         try:
@@ -628,7 +672,8 @@ def run_ours(args, world, rank, local):
         torch.cuda.empty_cache()
         extras = {"enc2b_35q": bench_enc2b(S, C, args, world, hbm_peak, peak_kind), "cut_48q": bench_cut(S, C),
                   "qft_32q": bench_qft(S, C, hbm_peak), "h_sweep_32q": bench_h_sweep(S, C, hbm_peak, peak_kind),
-                  "random_30q": bench_30q(S, C, hbm_peak), "expect_32q": bench_expect(S, C, hbm_peak)}
+                  "random_30q": bench_30q(S, C, hbm_peak), "expect_32q": bench_expect(S, C, hbm_peak),
+                  "ghz_sweep": bench_ghz_sweep(S, C)}
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "gates/s", "n_gpus": world, "steps": args.steps,

@@ -176,6 +176,163 @@ __global__ void __launch_bounds__(kExThreads) k_expect(const void *__restrict__ 
     for (int i = t; i < kExVals; i += kExThreads) partials[size_t(blockIdx.x) * kExVals + i] = acc[i];
 }
 
+// 2^13-amplitude tiles of complex64 (or decoded codes): each thread holds 32
+// amplitudes in registers and takes the pairs of five tile qubits at a time
+// (tile bits 8..12, then 3..7, then 0..2), three gathers from shared memory
+// instead of one sweep per qubit.  Shared layout j -> xswz(j): the load
+// (lanes along tile bits 0..4), the three gathers (lanes along bits 0..4;
+// 0,1,2,8,9; 5..9) and the code decode (lanes along bits 3..7) each touch
+// every bank the minimum number of times.
+__device__ __forceinline__ uint32_t xswz(uint32_t j) { return j ^ ((j >> 5) & 7u) ^ (((j >> 8) & 3u) << 3); }
+
+__device__ __forceinline__ unsigned long long pk2(float x, float y) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(x), "f"(y));
+    return r;
+}
+__device__ __forceinline__ void upk2(unsigned long long r, float &x, float &y) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(x), "=f"(y) : "l"(r));
+}
+__device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigned long long b, unsigned long long c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+// Register bits 0..NB-1 are tile bits B0..: for each, (Re, Im) of conj(p) q
+// over the pairs (packed FMAs: p.x (q.x, q.y) + p.y (q.y, -q.x)) into
+// v[3k], v[3k+1], and the probability of the registers with the bit set into
+// v[3k+2] (<sigma^z> = P - 2 P1 follows in the block sum).
+template <int B0, int NB>
+__device__ __forceinline__ void reg_pairs(const float2 (&x)[32], float (&v)[3 * kExMaxM + 1], bool total) {
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+        unsigned long long xy = pk2(v[3 * (B0 + b)], v[3 * (B0 + b) + 1]);
+#pragma unroll
+        for (int r = 0; r < 32; ++r) {
+            if (r >> b & 1) continue;
+            const float2 p = x[r], q = x[r | (1 << b)];
+            xy = fma2(pk2(p.x, p.x), pk2(q.x, q.y), xy);
+            xy = fma2(pk2(p.y, p.y), pk2(q.y, -q.x), xy);
+        }
+        upk2(xy, v[3 * (B0 + b)], v[3 * (B0 + b) + 1]);
+    }
+#pragma unroll
+    for (int r = 0; r < 32; ++r) {
+        const float pr = x[r].x * x[r].x + x[r].y * x[r].y;
+        if (total) v[3 * kExMaxM] += pr;
+#pragma unroll
+        for (int b = 0; b < NB; ++b)
+            if (r >> b & 1) v[3 * (B0 + b) + 2] += pr;
+    }
+}
+
+template <bool ENC>
+__global__ void __launch_bounds__(kExThreads, 2) k_expect13(const void *__restrict__ data,
+                                                            const float *__restrict__ scales, const ExpArgs a,
+                                                            double *__restrict__ partials) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    float2 *sm = reinterpret_cast<float2 *>(smem);
+    __shared__ double acc[kExVals];
+    __shared__ float red[kExWarps][3 * kExMaxM + 1];
+    __shared__ uint64_t gR[32];
+    __shared__ float tab[256];
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    for (int i = t; i < kExVals; i += kExThreads) acc[i] = 0.0;
+    for (int r = t; r < 32; r += kExThreads) {  // global offset of tile bits 8..12 of j = 256 r
+        uint64_t g = 0;
+        for (int q = 8; q < kExMaxM; ++q)
+            if ((r << 8) >> q & 1) g |= uint64_t(1) << a.tile_pos[q];
+        gR[r] = g;
+    }
+    for (int u = t; u < 256; u += kExThreads) {
+        const int q = int((signed char)u);
+        const int aq = q < 0 ? -q : q;
+        const float f = __fdiv_rn(float(aq > 127 ? 127 : aq), 127.0f);
+        tab[u] = q < 0 ? -f : f;
+    }
+    uint64_t gT = 0;  // global offset of tile bits 0..7 (= t)
+    for (int q = 0; q < 8; ++q)
+        if (t >> q & 1) gT |= uint64_t(1) << a.tile_pos[q];
+    __syncthreads();
+    for (uint64_t cta = blockIdx.x; cta < a.ntiles; cta += gridDim.x) {
+        if (!ENC) {
+            const float2 *psi = static_cast<const float2 *>(data);
+            uint64_t base = 0;
+            for (int o = 0; o < a.nouter; ++o) base |= ((cta >> o) & 1ull) << a.outer_pos[o];
+            // all 32 copies in flight (cp.async, 8 bytes each)
+#pragma unroll
+            for (int r = 0; r < 32; ++r) {
+                const uint32_t sa = uint32_t(__cvta_generic_to_shared(sm + xswz(uint32_t(t | (r << 8)))));
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(psi + (base | gT | gR[r]))
+                             : "memory");
+            }
+            asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+        } else {
+            const int4 *codes = static_cast<const int4 *>(data);
+            uint64_t bbase = 0;
+            for (int o = 0; o < a.nouter; ++o) bbase |= ((cta >> o) & 1ull) << (a.outer_pos[o] - kEncBlockLog2);
+            for (int bl = warp; bl < 32; bl += kExWarps) {
+                uint64_t b = bbase;
+                for (int q = 0; q < 5; ++q)
+                    if (bl >> q & 1) b |= uint64_t(1) << (a.tile_pos[kEncBlockLog2 + q] - kEncBlockLog2);
+                const int4 raw = codes[b * 32 + lane];
+                const float sc = scales[b];
+                const uint32_t w[4] = {uint32_t(raw.x), uint32_t(raw.y), uint32_t(raw.z), uint32_t(raw.w)};
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    const uint32_t word = w[e >> 1], sh = (e & 1) * 16;
+                    sm[xswz(uint32_t((bl << kEncBlockLog2) | (lane * 8 + e)))] =
+                        make_float2(__fmul_rn(sc, tab[(word >> sh) & 0xFFu]), __fmul_rn(sc, tab[(word >> (sh + 8)) & 0xFFu]));
+                }
+            }
+        }
+        __syncthreads();
+        float v[3 * kExMaxM + 1];
+#pragma unroll
+        for (int i = 0; i < 3 * kExMaxM + 1; ++i) v[i] = 0.0f;
+        float2 x[32];
+        // tile bits 8..12 in registers (j = t | r << 8); the tile's probability
+#pragma unroll
+        for (int r = 0; r < 32; ++r) x[r] = sm[xswz(uint32_t(t | (r << 8)))];
+        reg_pairs<8, 5>(x, v, true);
+        // tile bits 3..7 (j = (t & 7) | r << 3 | (t >> 3) << 8)
+#pragma unroll
+        for (int r = 0; r < 32; ++r) x[r] = sm[xswz(uint32_t((t & 7) | (r << 3) | ((t >> 3) << 8)))];
+        reg_pairs<3, 5>(x, v, false);
+        // tile bits 0..2 (j = r | t << 5; register bits 3, 4 were done above)
+#pragma unroll
+        for (int r = 0; r < 32; ++r) x[r] = sm[xswz(uint32_t(r | (t << 5)))];
+        reg_pairs<0, 3>(x, v, false);
+#pragma unroll
+        for (int i = 0; i < 3 * kExMaxM + 1; ++i) {
+            float s = v[i];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0) red[warp][i] = s;
+        }
+        __syncthreads();
+        if (t < 3 * kExMaxM) {
+            double s = 0.0;
+            for (int w = 0; w < kExWarps; ++w) s += double(red[w][t]);
+            if (t % 3 == 2) {  // P - 2 P1
+                double P = 0.0;
+                for (int w = 0; w < kExWarps; ++w) P += double(red[w][3 * kExMaxM]);
+                acc[t] += P - 2.0 * s;
+            } else {
+                acc[t] += 2.0 * s;
+            }
+        } else if (a.zouter && t >= 64 && t < 64 + a.nouter) {
+            const int o = t - 64;
+            double P = 0.0;
+            for (int w = 0; w < kExWarps; ++w) P += double(red[w][3 * kExMaxM]);
+            acc[3 * kExMaxM + o] += ((cta >> o) & 1ull) ? -P : P;
+        }
+        __syncthreads();
+    }
+    for (int i = t; i < kExVals; i += kExThreads) partials[size_t(blockIdx.x) * kExVals + i] = acc[i];
+}
+
 }  // namespace
 }  // namespace sv
 
@@ -211,6 +368,8 @@ extern "C" sv_status sv_expect_pauli(sv_handle h, double *out) {
             SV_CUDA_TRY(cudaFuncSetAttribute(k_expect<float2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
             SV_CUDA_TRY(cudaFuncSetAttribute(k_expect<double2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
             SV_CUDA_TRY(cudaFuncSetAttribute(k_expect<float2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+            SV_CUDA_TRY(cudaFuncSetAttribute(k_expect13<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+            SV_CUDA_TRY(cudaFuncSetAttribute(k_expect13<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
             configured = true;
         }
     }
@@ -239,7 +398,12 @@ extern "C" sv_status sv_expect_pauli(sv_handle h, double *out) {
         for (int q = 0; q < n; ++q)
             if (std::find(tile.begin(), tile.end(), q) == tile.end()) a.outer_pos[a.nouter++] = uint8_t(q);
         const void *data = h->data;
-        if (h->dt == SV_C64)
+        if (h->dt != SV_C128 && m == kExMaxM) {  // register segments (complex64, codes)
+            if (h->dt == SV_C64)
+                k_expect13<false><<<grid, kExThreads, smem, h->stream>>>(data, nullptr, a, d_part);
+            else
+                k_expect13<true><<<grid, kExThreads, smem, h->stream>>>(data, h->scales, a, d_part);
+        } else if (h->dt == SV_C64)
             k_expect<float2, false><<<grid, kExThreads, smem, h->stream>>>(data, nullptr, a, d_part);
         else if (h->dt == SV_C128)
             k_expect<double2, false><<<grid, kExThreads, smem, h->stream>>>(data, nullptr, a, d_part);

@@ -11,6 +11,8 @@ Cases (each a few GB of device memory at most, states larger than L2):
            (low, high and mixed qubits)
   cut      6x4 grid (24 qubits), depth 12, 8 cut CZs: 256 branches x 2
            batched halves of 2^12 amplitudes each
+  expect   28 qubits, uniform superposition, <sigma^alpha_i> of every qubit
+           (complex64; then the same from the two-byte code)
 """
 
 from __future__ import annotations
@@ -45,6 +47,13 @@ def main(case: str) -> None:
         u, _ = np.linalg.qr(z)
         for qs in ([0, 1, 2, 3, 4, 5], [20, 21, 22, 23, 24, 25], [3, 9, 14, 17, 21, 24]):
             s.apply_fused(qs, u)
+    elif case == "expect":
+        s = sv.StateVector(28, "c64")
+        s.run(C.uniform_circuit(28), "tiled")
+        s.expect_pauli()
+        e = sv.StateVector(28, "enc2b")
+        e.encode_from(s)
+        e.expect_pauli()
     elif case == "cut":
         c = C.grid_circuit(6, 4, 12, 1)
         sv.sv_cut_amplitudes(c, 24, C.grid_partition_mask(6, 4, 3), C.random_bitstrings(1024, 24, 7))
