@@ -531,6 +531,44 @@ def bench_ghz_sweep(S, C):
     return out
 
 
+def bench_cut42_depth(S, C):
+    """Decomposition at the paper's scale (Sec. 4, Fig. 4 workload shape): a
+    42-qubit 6x7 grid circuit cut between rows 0-2 and 3-5 (21 + 21 qubits)
+    at depths 4..14 (S = 7..14 cut gates), 1024 seeded amplitudes.  Branches
+    are summed in 2^p parts (p chosen so a half holds at most 2^31
+    amplitudes), one after another on this GPU.  Check: the projector and
+    Eq. 2 decompositions agree; the mean |amp|^2 times 2^42 is near 1."""
+    import numpy as np
+    import torch
+
+    n, mask = 42, C.grid_partition_mask(6, 7, 3)
+    z = C.random_bitstrings(1024, n, 7)
+    rows = {}
+    for depth in (4, 6, 8, 10, 12, 14):
+        c = C.grid_circuit(6, 7, depth, 1)
+        _, s = S.sv_cut_amplitudes(c, n, mask, z[:0])  # m = 0: counts the cut gates only
+        plog = max(0, 21 + s - 31)
+        res, first = {}, {}
+        for form in (0, 1):
+            for rep in range(2):  # the first run also compiles the passes
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                acc = np.zeros(z.size, dtype=np.complex128)
+                for part in range(1 << plog):
+                    a, _ = S.sv_cut_amplitudes_part(c, n, mask, z, part, plog, form=form)
+                    acc += a
+                torch.cuda.synchronize()
+                (first if rep == 0 else res)[form] = (acc, time.perf_counter() - t0)
+        a0, t = res[0]
+        a1, t1 = res[1]
+        rows[depth] = {"gates": len(c), "cut_gates": s, "parts": 1 << plog, "s_per_call": t,
+                       "ms_per_gate": 1e3 * t / len(c), "s_per_call_eq2": t1, "s_first_call_with_compile": first[0][1],
+                       "forms_max_rel_diff": float(np.max(np.abs(a0 - a1)) / np.max(np.abs(a0))),
+                       "mean_abs2_times_2^42": float(np.mean(np.abs(a0) ** 2) * 2.0 ** n)}
+    return {"workload": "6x7 grid (42 qubits), rows 0-2 | 3-5, 1024 amplitudes, branch parts summed in turn",
+            "by_depth": rows}
+
+
 def best_mode(S, state, circ):
     for mode in ("tiled", "fused", "pergate"):
         try:
@@ -673,7 +711,7 @@ def run_ours(args, world, rank, local):
         extras = {"enc2b_35q": bench_enc2b(S, C, args, world, hbm_peak, peak_kind), "cut_48q": bench_cut(S, C),
                   "qft_32q": bench_qft(S, C, hbm_peak), "h_sweep_32q": bench_h_sweep(S, C, hbm_peak, peak_kind),
                   "random_30q": bench_30q(S, C, hbm_peak), "expect_32q": bench_expect(S, C, hbm_peak),
-                  "ghz_sweep": bench_ghz_sweep(S, C)}
+                  "ghz_sweep": bench_ghz_sweep(S, C), "cut_42q_depth": bench_cut42_depth(S, C)}
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "gates/s", "n_gpus": world, "steps": args.steps,
