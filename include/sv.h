@@ -255,6 +255,21 @@ sv_status sv_cut_amplitudes(const char *text, int n, uint64_t maskA, int form, s
 sv_status sv_cut_amplitudes_part(const char *text, int n, uint64_t maskA, int form, uint64_t part, int nparts_log2,
                                  size_t m, const uint64_t *z, double *out, int *n_cut_out, void *stream);
 
+/* Eq. 3 over P partitions (Sec. 4: the sum over s of products of P
+ * circuits that each act on one partition, with memory bound by the largest
+ * partition's dimension).  part_of[q] in 0..P-1 gives the partition of each
+ * of the n qubits (2 <= n <= 128, 2 <= P <= 16, every partition nonempty and
+ * at most 40 qubits plus its cuts' branch bits).  Every CZ, CP or CX between
+ * two partitions is a decomposed gate; each partition holds the branch bits
+ * of the cuts that touch it.  z: m bit strings of ceil(n / 64) little-endian
+ * 64-bit words each (qubit q is bit q % 64 of word q / 64).  part and
+ * nparts_log2 as sv_cut_amplitudes_part (0, 0 for the whole sum).  Other
+ * arguments and errors as sv_cut_amplitudes; SV_ERR_UNSUPPORTED also when
+ * more than 16 branch bits are batched or a partition is too large. */
+sv_status sv_cut_amplitudes_multi(const char *text, int n, const uint8_t *part_of, int P, int form, uint64_t part,
+                                  int nparts_log2, size_t m, const uint64_t *z, double *out, int *n_cut_out,
+                                  void *stream);
+
 /* ---- host-only helpers (no GPU needed) -------------------------------------------- */
 
 /* The library's own matrix for a named gate of the circuit format: writes 8

@@ -1,17 +1,20 @@
-// Decomposition of entangling gates across a partition (Sec. 4, Eq. 2-3).
+// Decomposition of entangling gates across partitions (Sec. 4, Eq. 2-3).
 //
-// Rewrite (host): qubits in maskA form partition A, the others B.  Every CZ or
-// CP between A and B becomes a branch slot k; a CX between them is first
-// written as H CZ H on its target.  Decomposition forms:
+// Rewrite (host): the qubits fall into P partitions.  Every CZ or CP between
+// two partitions becomes a branch slot k; a CX between them is first written
+// as H CZ H on its target.  Decomposition forms (a = the gate's first qubit,
+// b = its second):
 //   projector: CP_ab(th) = P0(a) (x) 1 + P1(a) (x) P(th)(b)   (weight 1)
 //   Eq. 2:     CZ_ab = 1/2 sum_{s=+-1} D_s(a) (x) D_s(b),
 //              D_s = exp(i sigma^z (x s - pi/4)), cos 2x = i  (weight 1/2 each)
-// so the circuit is a sum over s in {0,1}^S of a product of an A-only and a
-// B-only circuit (Sec. 4), and <z|C|0> = sum_s <z_A|W_A(s)|0><z_B|W_B(s)|0>
-// (Eq. 3).
+// so the circuit is a sum over s in {0,1}^S of a product of circuits that
+// each act on one partition (Sec. 4), and <z|C|0> = sum_s prod_p
+// <z_p|W_p(s)|0_p> (Eq. 3).  W_p depends only on the bits of the cuts that
+// touch partition p.
 //
-// Batched simulation (GPU): for each half p the 2^S branch vectors are one
-// vector of 2^(n_p + S) complex64 amplitudes whose top S index bits are s.
+// Batched simulation (GPU): for each partition p the branch vectors are one
+// vector of 2^(n_p + S_p) complex64 amplitudes whose top index bits are the
+// S_p branch bits of the cuts touching p.
 // A branch operator is then an ordinary diagonal gate coupling a half's qubit
 // to branch bit k (the projector zeroes amplitudes where bit a != s_k; P(th)
 // and D_s are phases selected by (bit, s_k)).  Branch bits only ever appear
@@ -21,8 +24,9 @@
 // (or, with branch-prefix sharing, the branches are forked from branch 0 at
 // their first operator, see run_half).
 //
-// Sum (GPU): one warp per output bit string, lanes over s, products and sum
-// in FP64, times the weight.
+// Sum (GPU): one warp per output bit string (its partition indices gathered
+// from the string's bits by the first P lanes), lanes over s, products of the
+// P partitions' amplitudes and the sum in FP64, times the weight.
 #include <complex>
 #include <cstdlib>
 #include <vector>
@@ -41,27 +45,56 @@ __global__ void k_branch_init(float2 *psi, int np, int S) {
         psi[s << np] = make_float2(1.0f, 0.0f);
 }
 
-__global__ void k_branch_sum(const float2 *__restrict__ A, const float2 *__restrict__ B, int nA, int nB, int S,
-                             const uint64_t *__restrict__ zA, const uint64_t *__restrict__ zB, size_t m, double w,
-                             double2 *__restrict__ out) {
+constexpr int kMaxParts = 16;
+constexpr int kMaxPartQubits = 40;  // a partition's state, like any state
+constexpr int kMaxCutBits = 24;     // branch bits of one partition
+constexpr int kMaxCutQubits = 128;  // qubits of the circuit
+
+struct CutSumArgs {
+    int P, Sv, nwords;
+    uint64_t m;
+    double w;
+    const float2 *vec[kMaxParts];
+    int nlocal[kMaxParts], nbits[kMaxParts];
+    uint8_t cutbit[kMaxParts][kMaxCutBits];      // partition bit j <- batched branch bit cutbit[p][j]
+    uint8_t qubit[kMaxParts][kMaxPartQubits];    // partition qubit i <- circuit qubit qubit[p][i]
+};
+
+__global__ void k_cut_sum(const uint64_t *__restrict__ z, const CutSumArgs a, double2 *__restrict__ out) {
     const int lane = threadIdx.x & 31;
     const size_t warps = size_t(gridDim.x) * (blockDim.x >> 5);
-    const uint64_t ns = uint64_t(1) << S;
-    for (size_t j = size_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); j < m; j += warps) {
-        const uint64_t za = zA[j], zb = zB[j];
+    const uint64_t ns = uint64_t(1) << a.Sv;
+    for (size_t j = size_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); j < a.m; j += warps) {
+        // lane p < P: the index of z_j inside partition p
+        uint64_t mine = 0;
+        if (lane < a.P)
+            for (int i = 0; i < a.nlocal[lane]; ++i) {
+                const int q = a.qubit[lane][i];
+                mine |= ((z[j * a.nwords + (q >> 6)] >> (q & 63)) & 1ull) << i;
+            }
+        uint64_t zl[kMaxParts];
+#pragma unroll
+        for (int p = 0; p < kMaxParts; ++p) zl[p] = __shfl_sync(0xffffffffu, mine, p);
         double re = 0.0, im = 0.0;
         for (uint64_t s = lane; s < ns; s += 32) {
-            const float2 a = A[(s << nA) | za], b = B[(s << nB) | zb];
-            const double ar = a.x, ai = a.y, br = b.x, bi = b.y;
-            re += ar * br - ai * bi;
-            im += ar * bi + ai * br;
+            double pr = 1.0, pi = 0.0;
+            for (int p = 0; p < a.P; ++p) {
+                uint64_t sp = 0;
+                for (int k = 0; k < a.nbits[p]; ++k) sp |= ((s >> a.cutbit[p][k]) & 1ull) << k;
+                const float2 v = a.vec[p][(sp << a.nlocal[p]) | zl[p]];
+                const double r = pr * v.x - pi * v.y;
+                pi = pr * v.y + pi * v.x;
+                pr = r;
+            }
+            re += pr;
+            im += pi;
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             re += __shfl_xor_sync(0xffffffffu, re, o);
             im += __shfl_xor_sync(0xffffffffu, im, o);
         }
-        if (lane == 0) out[j] = make_double2(w * re, w * im);
+        if (lane == 0) out[j] = make_double2(a.w * re, a.w * im);
     }
 }
 
@@ -95,10 +128,13 @@ void append_lowered(const Instr &ins, std::vector<PGate> *out) {
     out->insert(out->end(), g.begin(), g.end());
 }
 
-struct Half {
+struct Half {            // one partition
     int nlocal = 0;     // qubits of the partition
+    int nbits = 0;      // batched branch bits of the cuts touching it
     int nq = 0;         // qubits of the batched vector (local + branch, padded to a tile)
     std::vector<PGate> gates;
+    std::vector<int> qubits;   // circuit qubit of local qubit i
+    std::vector<int> cutbits;  // batched branch bit of partition bit j
     float2 *d = nullptr;
 };
 
@@ -183,21 +219,35 @@ using namespace sv;
 
 // Sum over the branches s with s mod 2^plog == part (plog = 0: all of them).
 // The low plog branch bits are then fixed: their branch operators are plain
-// diagonal gates on the halves' qubits, and only the other S - plog bits are
-// batched.
-static sv_status cut_impl(const char *text, int n, uint64_t maskA, int form, uint64_t part, int plog, size_t m,
-                          const uint64_t *z, double *out, int *n_cut_out, void *stream) {
-    if (n < 2 || n > 64 || (form != 0 && form != 1) || (m > 0 && (!z || !out))) {
-        set_error("bad arguments (n=%d, form=%d)", n, form);
+// diagonal gates on the partitions' qubits, and only the other S - plog bits
+// are batched.  z: m bit strings of nwords 64-bit words (qubit q is bit q % 64
+// of word q / 64).
+static sv_status cut_impl(const char *text, int n, const uint8_t *part_of, int P, int form, uint64_t part, int plog,
+                          size_t m, const uint64_t *z, int nwords, double *out, int *n_cut_out, void *stream) {
+    if (n < 2 || n > kMaxCutQubits || P < 2 || P > kMaxParts || !part_of || (form != 0 && form != 1) ||
+        nwords != (n + 63) / 64 || (m > 0 && (!z || !out))) {
+        set_error("bad arguments (n=%d, P=%d, form=%d, nwords=%d)", n, P, form, nwords);
         return SV_ERR_ARG;
     }
-    const uint64_t all = n == 64 ? ~uint64_t(0) : ((uint64_t(1) << n) - 1);
-    if ((maskA & all) == 0 || (maskA & all) == all || (maskA & ~all)) {
-        set_error("maskA must select a proper, nonempty subset of the %d qubits", n);
-        return SV_ERR_ARG;
+    Half parts[kMaxParts];
+    int side[kMaxCutQubits], loc[kMaxCutQubits];
+    for (int q = 0; q < n; ++q) {
+        if (part_of[q] >= P) {
+            set_error("qubit %d: partition %d outside 0..%d", q, int(part_of[q]), P - 1);
+            return SV_ERR_ARG;
+        }
+        side[q] = part_of[q];
+        loc[q] = parts[side[q]].nlocal++;
+        parts[side[q]].qubits.push_back(q);
     }
+    for (int p = 0; p < P; ++p)
+        if (parts[p].nlocal == 0) {
+            set_error("partition %d has no qubits", p);
+            return SV_ERR_ARG;
+        }
+    const int top = n - 64 * (nwords - 1);  // qubits in the last word
     for (size_t j = 0; j < m; ++j)
-        if (z[j] & ~all) {
+        if (top < 64 && (z[j * nwords + nwords - 1] >> top)) {
             set_error("bit string %zu has bits above qubit %d", j, n - 1);
             return SV_ERR_ARG;
         }
@@ -205,28 +255,22 @@ static sv_status cut_impl(const char *text, int n, uint64_t maskA, int form, uin
     sv_status s = parse_circuit(text, n, &c);
     if (s) return s;
 
-    int side[64], loc[64];
-    Half half[2];
-    for (int q = 0; q < n; ++q) {
-        side[q] = (maskA >> q & 1) ? 0 : 1;
-        loc[q] = half[side[q]].nlocal++;
-    }
-    // count the decomposed gates first (branch bits sit above the local qubits)
+    // count the decomposed gates first
     int S = 0;
     for (const Instr &ins : c.instrs) {
         if (ins.nq != 2 || side[ins.q[0]] == side[ins.q[1]]) continue;
         if (ins.name == "SWAP") {
-            set_error("a SWAP across the partition cannot be decomposed");
+            set_error("a SWAP across partitions cannot be decomposed");
             return SV_ERR_UNSUPPORTED;
         }
         if (form == 1 && ins.name == "CP") {
-            set_error("the Eq. 2 form decomposes CZ only (CP across the partition)");
+            set_error("the Eq. 2 form decomposes CZ only (CP across partitions)");
             return SV_ERR_UNSUPPORTED;
         }
         ++S;
     }
-    if (S > 16) {
-        set_error("%d decomposed gates (at most 16)", S);
+    if (S - plog > 16) {
+        set_error("%d decomposed gates, %d of them batched (at most 16)", S, S - plog);
         return SV_ERR_UNSUPPORTED;
     }
     const int Svar = S > plog ? S - plog : 0;  // batched branch bits
@@ -235,45 +279,50 @@ static sv_status cut_impl(const char *text, int n, uint64_t maskA, int form, uin
         for (size_t j = 0; j < 2 * m; ++j) out[j] = 0.0;
         return SV_OK;
     }
-    for (int p = 0; p < 2; ++p) {
-        half[p].nq = half[p].nlocal + Svar < kTileM64 ? kTileM64 : half[p].nlocal + Svar;
-        if (half[p].nq > kMaxQubits) {
-            set_error("half %d needs %d qubits (local %d + %d branch bits)", p, half[p].nq, half[p].nlocal, Svar);
-            return SV_ERR_UNSUPPORTED;
-        }
-    }
+    // branch operators: a Z-basis projector (or Eq. 2 phase) on the first
+    // qubit's partition, the phase on the second's, conditioned on the cut's
+    // branch bit, which each partition holds above its own qubits
     int k = 0;
     for (const Instr &ins0 : c.instrs) {
         Instr ins = ins0;
         if (ins.nq == 1 || side[ins.q[0]] == side[ins.q[1]]) {
             const int p = side[ins.q[0]];
             for (int j = 0; j < ins.nq; ++j) ins.q[j] = loc[ins.q[j]];
-            append_lowered(ins, &half[p].gates);
+            append_lowered(ins, &parts[p].gates);
             continue;
         }
-        const int a = ins.q[0], b = ins.q[1];
+        const int qa = ins.q[0], qb = ins.q[1];
+        Half &A = parts[side[qa]], &B = parts[side[qb]];
         const double theta = ins.name == "CP" ? ins.p[0] : 3.14159265358979323846;
         Instr h;
         h.name = "H";
         h.nq = 1;
         if (ins.name == "CX") {  // CX = H_t CZ H_t
-            h.q[0] = loc[b];
-            append_lowered(h, &half[side[b]].gates);
+            h.q[0] = loc[qb];
+            append_lowered(h, &B.gates);
         }
-        const int qa = side[a] == 0 ? a : b, qb = side[a] == 0 ? b : a;
         const uint64_t la = uint64_t(1) << loc[qa], lb = uint64_t(1) << loc[qb];
         const bool fixed = k < plog;
         const int sfix = int((part >> k) & 1);
-        const uint64_t ka = fixed ? 0 : uint64_t(1) << (half[0].nlocal + k - plog);
-        const uint64_t kb = fixed ? 0 : uint64_t(1) << (half[1].nlocal + k - plog);
+        uint64_t ka = 0, kb = 0;
+        if (!fixed) {
+            if (A.nbits >= kMaxCutBits || B.nbits >= kMaxCutBits) {
+                set_error("a partition touches more than %d batched cuts", kMaxCutBits);
+                return SV_ERR_UNSUPPORTED;
+            }
+            A.cutbits.push_back(k - plog);
+            B.cutbits.push_back(k - plog);
+            ka = uint64_t(1) << (A.nlocal + A.nbits++);
+            kb = uint64_t(1) << (B.nlocal + B.nbits++);
+        }
         if (form == 0) {
             if (fixed) {
-                half[0].gates.push_back(phase_gate(la, sfix ? 0 : la, 0.0));  // keep bit a == s_k
-                if (sfix) half[1].gates.push_back(phase_gate(lb, lb, std::polar(1.0, theta)));
+                A.gates.push_back(phase_gate(la, sfix ? 0 : la, 0.0));  // keep bit a == s_k
+                if (sfix) B.gates.push_back(phase_gate(lb, lb, std::polar(1.0, theta)));
             } else {
-                half[0].gates.push_back(phase_gate(la | ka, la, 0.0));  // bit a = 1, s_k = 0: P0 removes it
-                half[0].gates.push_back(phase_gate(la | ka, ka, 0.0));  // bit a = 0, s_k = 1: P1 removes it
-                half[1].gates.push_back(phase_gate(lb | kb, lb | kb, std::polar(1.0, theta)));
+                A.gates.push_back(phase_gate(la | ka, la, 0.0));  // bit a = 1, s_k = 0: P0 removes it
+                A.gates.push_back(phase_gate(la | ka, ka, 0.0));  // bit a = 0, s_k = 1: P1 removes it
+                B.gates.push_back(phase_gate(lb | kb, lb | kb, std::polar(1.0, theta)));
             }
         } else {
             for (int sb = 0; sb < 2; ++sb) {
@@ -281,24 +330,33 @@ static sv_status cut_impl(const char *text, int n, uint64_t maskA, int form, uin
                 cd d[2];
                 eq2_diag(sb, d);
                 const uint64_t sva = sb ? ka : 0, svb = sb ? kb : 0;
-                half[0].gates.push_back(phase_gate(la | ka, sva, d[0]));
-                half[0].gates.push_back(phase_gate(la | ka, la | sva, d[1]));
-                half[1].gates.push_back(phase_gate(lb | kb, svb, d[0]));
-                half[1].gates.push_back(phase_gate(lb | kb, lb | svb, d[1]));
+                A.gates.push_back(phase_gate(la | ka, sva, d[0]));
+                A.gates.push_back(phase_gate(la | ka, la | sva, d[1]));
+                B.gates.push_back(phase_gate(lb | kb, svb, d[0]));
+                B.gates.push_back(phase_gate(lb | kb, lb | svb, d[1]));
             }
         }
-        if (ins.name == "CX") append_lowered(h, &half[side[b]].gates);
+        if (ins.name == "CX") append_lowered(h, &B.gates);
         ++k;
+    }
+    for (int p = 0; p < P; ++p) {
+        Half &h = parts[p];
+        h.nq = h.nlocal + h.nbits < kTileM64 ? kTileM64 : h.nlocal + h.nbits;
+        if (h.nlocal > kMaxPartQubits || h.nq > kMaxQubits) {
+            set_error("partition %d needs %d qubits (local %d + %d branch bits)", p, h.nq, h.nlocal, h.nbits);
+            return SV_ERR_UNSUPPORTED;
+        }
     }
     if (m == 0) return SV_OK;
 
-    // device memory: two batched vectors + bit strings + results
-    const size_t bytesA = sizeof(float2) << half[0].nq, bytesB = sizeof(float2) << half[1].nq;
-    const size_t bytesZ = 2 * m * sizeof(uint64_t), bytesO = m * sizeof(double2);
+    // device memory: the batched vectors + bit strings + results
+    size_t bytesV = 0;
+    for (int p = 0; p < P; ++p) bytesV += sizeof(float2) << parts[p].nq;
+    const size_t bytesZ = m * size_t(nwords) * sizeof(uint64_t), bytesO = m * sizeof(double2);
     size_t free_b = 0, total_b = 0;
     SV_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
-    if (bytesA + bytesB + bytesZ + bytesO + (size_t(256) << 20) > free_b) {
-        set_error("decomposition needs %zu bytes of device memory, %zu free", bytesA + bytesB + bytesZ + bytesO, free_b);
+    if (bytesV + bytesZ + bytesO + (size_t(256) << 20) > free_b) {
+        set_error("decomposition needs %zu bytes of device memory, %zu free", bytesV + bytesZ + bytesO, free_b);
         return SV_ERR_OOM;
     }
     if (fault_injected("alloc")) {
@@ -308,43 +366,43 @@ static sv_status cut_impl(const char *text, int n, uint64_t maskA, int form, uin
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     uint64_t *dz = nullptr;
     double2 *dout = nullptr;
-    std::vector<uint64_t> zs(2 * m);
-    for (size_t j = 0; j < m; ++j) {
-        uint64_t za = 0, zb = 0;
-        for (int q = 0; q < n; ++q) {
-            const uint64_t bit = (z[j] >> q) & 1;
-            if (side[q] == 0) za |= bit << loc[q];
-            else zb |= bit << loc[q];
-        }
-        zs[j] = za;
-        zs[m + j] = zb;
-    }
     auto release = [&]() {
         cudaStreamSynchronize(st);
-        for (Half &h : half)
-            if (h.d) cudaFree(h.d);
+        for (int p = 0; p < P; ++p)
+            if (parts[p].d) cudaFree(parts[p].d);
         if (dz) cudaFree(dz);
         if (dout) cudaFree(dout);
     };
-    cudaError_t e = cudaMalloc(&half[0].d, bytesA);
-    if (e == cudaSuccess) e = cudaMalloc(&half[1].d, bytesB);
+    cudaError_t e = cudaSuccess;
+    for (int p = 0; p < P && e == cudaSuccess; ++p) e = cudaMalloc(&parts[p].d, sizeof(float2) << parts[p].nq);
     if (e == cudaSuccess) e = cudaMalloc(&dz, bytesZ);
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&dout), bytesO);
     if (e != cudaSuccess) {
         release();
         return cuda_status(e, "cudaMalloc (decomposition)");
     }
-    for (int p = 0; p < 2 && s == SV_OK; ++p) s = run_half(half[p], st, Svar);
+    for (int p = 0; p < P && s == SV_OK; ++p) s = run_half(parts[p], st, parts[p].nbits);
     if (s == SV_OK) {
-        e = cudaMemcpyAsync(dz, zs.data(), bytesZ, cudaMemcpyHostToDevice, st);
+        e = cudaMemcpyAsync(dz, z, bytesZ, cudaMemcpyHostToDevice, st);
         if (e != cudaSuccess) s = cuda_status(e, "cudaMemcpyAsync");
     }
     if (s == SV_OK) {
-        const double w = form == 1 ? std::ldexp(1.0, -S) : 1.0;
+        CutSumArgs a{};
+        a.P = P;
+        a.Sv = Svar;
+        a.nwords = nwords;
+        a.m = m;
+        a.w = form == 1 ? std::ldexp(1.0, -S) : 1.0;
+        for (int p = 0; p < P; ++p) {
+            a.vec[p] = parts[p].d;
+            a.nlocal[p] = parts[p].nlocal;
+            a.nbits[p] = parts[p].nbits;
+            for (int j = 0; j < parts[p].nbits; ++j) a.cutbit[p][j] = uint8_t(parts[p].cutbits[size_t(j)]);
+            for (int i = 0; i < parts[p].nlocal; ++i) a.qubit[p][i] = uint8_t(parts[p].qubits[size_t(i)]);
+        }
         const size_t blocks = (m + 7) / 8 < 4096 ? (m + 7) / 8 : 4096;
-        k_branch_sum<<<unsigned(blocks), 256, 0, st>>>(half[0].d, half[1].d, half[0].nlocal, half[1].nlocal, Svar, dz,
-                                                       dz + m, m, w, dout);
-        s = check_launch(cudaGetLastError(), "k_branch_sum");
+        k_cut_sum<<<unsigned(blocks), 256, 0, st>>>(dz, a, dout);
+        s = check_launch(cudaGetLastError(), "k_cut_sum");
     }
     if (s == SV_OK) {
         e = cudaMemcpyAsync(out, dout, bytesO, cudaMemcpyDeviceToHost, st);
@@ -355,9 +413,26 @@ static sv_status cut_impl(const char *text, int n, uint64_t maskA, int form, uin
     return s;
 }
 
+// Two partitions given by a mask (partition 0 = the mask's qubits).
+static sv_status cut_mask(const char *text, int n, uint64_t maskA, int form, uint64_t part, int plog, size_t m,
+                          const uint64_t *z, double *out, int *n_cut_out, void *stream) {
+    if (n < 2 || n > 64) {
+        set_error("n = %d outside 2..64 (sv_cut_amplitudes_multi takes up to %d qubits)", n, kMaxCutQubits);
+        return SV_ERR_ARG;
+    }
+    const uint64_t all = n == 64 ? ~uint64_t(0) : ((uint64_t(1) << n) - 1);
+    if ((maskA & all) == 0 || (maskA & all) == all || (maskA & ~all)) {
+        set_error("maskA must select a proper, nonempty subset of the %d qubits", n);
+        return SV_ERR_ARG;
+    }
+    uint8_t part_of[64];
+    for (int q = 0; q < n; ++q) part_of[q] = (maskA >> q & 1) ? 0 : 1;
+    return cut_impl(text, n, part_of, 2, form, part, plog, m, z, 1, out, n_cut_out, stream);
+}
+
 extern "C" sv_status sv_cut_amplitudes(const char *text, int n, uint64_t maskA, int form, size_t m, const uint64_t *z,
                                        double *out, int *n_cut_out, void *stream) {
-    return cut_impl(text, n, maskA, form, 0, 0, m, z, out, n_cut_out, stream);
+    return cut_mask(text, n, maskA, form, 0, 0, m, z, out, n_cut_out, stream);
 }
 
 extern "C" sv_status sv_cut_amplitudes_part(const char *text, int n, uint64_t maskA, int form, uint64_t part,
@@ -367,5 +442,15 @@ extern "C" sv_status sv_cut_amplitudes_part(const char *text, int n, uint64_t ma
         set_error("bad part %llu of 2^%d", (unsigned long long)part, nparts_log2);
         return SV_ERR_ARG;
     }
-    return cut_impl(text, n, maskA, form, part, nparts_log2, m, z, out, n_cut_out, stream);
+    return cut_mask(text, n, maskA, form, part, nparts_log2, m, z, out, n_cut_out, stream);
+}
+
+extern "C" sv_status sv_cut_amplitudes_multi(const char *text, int n, const uint8_t *part_of, int P, int form,
+                                             uint64_t part, int nparts_log2, size_t m, const uint64_t *z,
+                                             double *out, int *n_cut_out, void *stream) {
+    if (nparts_log2 < 0 || nparts_log2 > 16 || (part >> nparts_log2) != 0) {
+        set_error("bad part %llu of 2^%d", (unsigned long long)part, nparts_log2);
+        return SV_ERR_ARG;
+    }
+    return cut_impl(text, n, part_of, P, form, part, nparts_log2, m, z, (n + 63) / 64, out, n_cut_out, stream);
 }

@@ -66,6 +66,9 @@ SIGNATURES = {
                                 _u64p, _dp, _ip, _vp]),
     "sv_cut_amplitudes_part": (_st, [ctypes.c_char_p, ctypes.c_int, ctypes.c_uint64, ctypes.c_int, ctypes.c_uint64,
                                      ctypes.c_int, ctypes.c_size_t, _u64p, _dp, _ip, _vp]),
+    "sv_cut_amplitudes_multi": (_st, [ctypes.c_char_p, ctypes.c_int, ctypes.POINTER(ctypes.c_uint8), ctypes.c_int,
+                                      ctypes.c_int, ctypes.c_uint64, ctypes.c_int, ctypes.c_size_t, _u64p, _dp,
+                                      ctypes.POINTER(ctypes.c_int), _vp]),
     "sv_gate_matrix": (ctypes.c_int, [ctypes.c_char_p, _dp, ctypes.c_int, _dp]),
     "sv_version": (ctypes.c_char_p, []),
 }
@@ -174,6 +177,26 @@ def sv_cut_amplitudes_part(circuit, n: int, mask_a: int, z, part: int, nparts_lo
     _check(lib().sv_cut_amplitudes_part(_text(circuit), n, ctypes.c_uint64(mask_a), form, ctypes.c_uint64(part),
                                         nparts_log2, zz.size, zz.ctypes.data_as(_u64p), _dptr(out), ctypes.byref(s),
                                         _vp(st)), "sv_cut_amplitudes_part")
+    return out.view(np.complex128).copy(), s.value
+
+
+def sv_cut_amplitudes_multi(circuit, n: int, part_of, z_words, form: int = 0, part: int = 0, nparts_log2: int = 0,
+                            stream=None):
+    """Eq. 3 over P partitions (part_of[q] = partition of qubit q); z_words:
+    (m, ceil(n/64)) uint64 bit strings, qubit q = bit q % 64 of word q // 64.
+    Returns (amplitudes complex128[m], S)."""
+    import torch
+
+    po = np.ascontiguousarray(part_of, dtype=np.uint8)
+    zz = np.ascontiguousarray(z_words, dtype=np.uint64).reshape(-1, (n + 63) // 64)
+    m = zz.shape[0]
+    out = np.zeros(2 * m, dtype=np.float64)
+    s = ctypes.c_int(0)
+    st = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+    _check(lib().sv_cut_amplitudes_multi(_text(circuit), n, po.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                                         int(po.max()) + 1, form, ctypes.c_uint64(part), nparts_log2, m,
+                                         zz.ctypes.data_as(_u64p), _dptr(out), ctypes.byref(s), _vp(st)),
+           "sv_cut_amplitudes_multi")
     return out.view(np.complex128).copy(), s.value
 
 
