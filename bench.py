@@ -569,6 +569,36 @@ def bench_cut42_depth(S, C):
             "by_depth": rows}
 
 
+def bench_ghz128(S, C):
+    """The paper's largest decomposition run (Sec. 4): the 128-qubit GHZ chain
+    (H(0), CNOT(i, i+1)) in 8 partitions of 16 qubits (7 decomposed CNOTs),
+    M = 2^27 coefficients: the first 2^27 - 1 basis states and |1...1>.
+    <0...0|C|0> and <1...1|C|0> must be 1/sqrt(2), every other one 0."""
+    import math
+
+    import numpy as np
+    import torch
+
+    n, m = 128, 1 << 27
+    z = np.zeros((m, 2), dtype=np.uint64)
+    z[: m - 1, 0] = np.arange(m - 1, dtype=np.uint64)
+    z[m - 1] = np.uint64(0xFFFFFFFFFFFFFFFF)
+    part_of = [q // 16 for q in range(n)]
+    c = C.ghz_circuit(n)
+    S.sv_cut_amplitudes_multi(c, n, part_of, z[:1024])  # compiles the passes
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    amps, s = S.sv_cut_amplitudes_multi(c, n, part_of, z)
+    torch.cuda.synchronize()
+    t = time.perf_counter() - t0
+    h = 1 / math.sqrt(2)
+    return {"workload": "GHZ chain, 128 qubits, 8 partitions x 16, M = 2^27 coefficients", "cut_gates": s,
+            "s_per_call": t, "coefficients_per_s": m / t,
+            "amp_0": [float(amps[0].real), float(amps[0].imag)], "amp_1s": [float(amps[-1].real), float(amps[-1].imag)],
+            "max_err_vs_paper": float(max(abs(amps[0] - h), abs(amps[-1] - h), np.max(np.abs(amps[1:-1])))),
+            "note": "end to end: host bit strings (2 GiB) in, 2^27 complex128 out"}
+
+
 def best_mode(S, state, circ):
     for mode in ("tiled", "fused", "pergate"):
         try:
@@ -711,7 +741,8 @@ def run_ours(args, world, rank, local):
         extras = {"enc2b_35q": bench_enc2b(S, C, args, world, hbm_peak, peak_kind), "cut_48q": bench_cut(S, C),
                   "qft_32q": bench_qft(S, C, hbm_peak), "h_sweep_32q": bench_h_sweep(S, C, hbm_peak, peak_kind),
                   "random_30q": bench_30q(S, C, hbm_peak), "expect_32q": bench_expect(S, C, hbm_peak),
-                  "ghz_sweep": bench_ghz_sweep(S, C), "cut_42q_depth": bench_cut42_depth(S, C)}
+                  "ghz_sweep": bench_ghz_sweep(S, C), "cut_42q_depth": bench_cut42_depth(S, C),
+                  "ghz128_m2e27": bench_ghz128(S, C)}
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "gates/s", "n_gpus": world, "steps": args.steps,
