@@ -142,5 +142,8 @@ const char *tile_kernel_name(const sv_state *h);
 std::string tile_codegen_key();
 // Planner lookahead width (SV_PLAN_LOOKAHEAD, default 4; 0 = greedy).
 int plan_lookahead_width();
+// Segment (register set) lookahead width (SV_SEG_LOOKAHEAD, default 4; 0 =
+// first fit).
+int seg_lookahead_width();
 
 }  // namespace sv

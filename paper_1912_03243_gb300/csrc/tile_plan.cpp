@@ -301,7 +301,90 @@ uint64_t choose_tile_lookahead(const std::vector<PGate> &G, const std::vector<in
     return best;
 }
 
+// Register qubits of the next segment, first fit: pending gates in order
+// add their non-diagonal qubits while at most rb fit.
+uint64_t rset_first_fit(const std::vector<PGate> &G, const std::vector<int> &pending, int rb) {
+    uint64_t Rset = 0, bF = 0, bD = 0;
+    for (int idx : pending) {
+        const PGate &g = G[size_t(idx)];
+        const uint64_t F = full_of(g), D = diag_of(g);
+        if (conflicts(F, D, bF, bD)) {
+            bF |= F;
+            bD |= D;
+            continue;
+        }
+        const uint64_t need = F & ~Rset;
+        if (popc(Rset | need) <= rb) Rset |= need;
+        else {
+            bF |= F;
+            bD |= D;
+        }
+    }
+    return Rset;
+}
+
+// Segments first fit needs for `pending` (diagonal gates count as free).
+int segments_first_fit(const std::vector<PGate> &G, std::vector<int> pending, int rb, uint64_t all) {
+    int ns = 0;
+    for (;;) {
+        bool nondiag = false;
+        for (int idx : pending) nondiag |= G[size_t(idx)].kind == 0;
+        if (!nondiag) return ns;
+        take_pass(G, pending, rset_first_fit(G, pending, rb), all);
+        ++ns;
+    }
+}
+
+// Register qubits of the next segment with lookahead: first fit, and greedy
+// growth by applicable-gate count started from each of the `width` best
+// single qubits; each candidate is rolled out with first fit and the one
+// needing the fewest segments wins (ties: first fit, then more gates now).
+uint64_t rset_lookahead(const std::vector<PGate> &G, const std::vector<int> &pending, uint64_t T, int rb, uint64_t all,
+                        int width) {
+    std::vector<uint64_t> cand{rset_first_fit(G, pending, rb)};
+    std::vector<std::pair<int, int>> first;
+    for (int q = 0; q < 64; ++q)
+        if (T >> q & 1) first.push_back({count_applicable(G, pending, uint64_t(1) << q, all), q});
+    std::sort(first.begin(), first.end(),
+              [](auto a, auto b) { return a.first > b.first || (a.first == b.first && a.second < b.second); });
+    for (int i = 0; i < width && i < int(first.size()); ++i) {
+        uint64_t R = uint64_t(1) << first[size_t(i)].second;
+        while (popc(R) < rb && popc(R) < popc(T)) {
+            int best_q = -1, best_c = -1;
+            for (int q = 0; q < 64; ++q) {
+                if (!(T >> q & 1) || (R >> q & 1)) continue;
+                const int c = count_applicable(G, pending, R | (uint64_t(1) << q), all);
+                if (c > best_c) {
+                    best_c = c;
+                    best_q = q;
+                }
+            }
+            R |= uint64_t(1) << best_q;
+        }
+        if (std::find(cand.begin(), cand.end(), R) == cand.end()) cand.push_back(R);
+    }
+    uint64_t best = cand[0];
+    int best_ns = 1 << 30, best_cnt = -1;
+    for (uint64_t R : cand) {
+        std::vector<int> rest = pending;
+        take_pass(G, rest, R, all);
+        const int ns = 1 + segments_first_fit(G, rest, rb, all);
+        const int cnt = int(pending.size() - rest.size());
+        if (ns < best_ns || (ns == best_ns && R != cand[0] && best != cand[0] && cnt > best_cnt)) {
+            best_ns = ns;
+            best_cnt = cnt;
+            best = R;
+        }
+    }
+    return best;
+}
+
 }  // namespace
+
+int seg_lookahead_width() {
+    static const int width = std::getenv("SV_SEG_LOOKAHEAD") ? std::atoi(std::getenv("SV_SEG_LOOKAHEAD")) : 4;
+    return width;
+}
 
 int tile_rb64() {
     const char *e = std::getenv("SV_TILE_RB");
@@ -407,23 +490,8 @@ sv_status plan_tiles(const std::vector<PGate> &G, int n, const TileConfig &cfg, 
             since_flush = 0;
         };
         while (!remaining.empty()) {
-            uint64_t Rset = 0;
-            bF = bD = 0;
-            for (int idx : remaining) {
-                const PGate &g = G[size_t(idx)];
-                const uint64_t F = full_of(g), D = diag_of(g);
-                if (conflicts(F, D, bF, bD)) {
-                    bF |= F;
-                    bD |= D;
-                    continue;
-                }
-                const uint64_t need = F & ~Rset;
-                if (popc(Rset | need) <= rb) Rset |= need;
-                else {
-                    bF |= F;
-                    bD |= D;
-                }
-            }
+            const int sw = seg_lookahead_width();
+            uint64_t Rset = sw > 0 ? rset_lookahead(G, remaining, T, rb, all, sw) : rset_first_fit(G, remaining, rb);
             for (int k = 0; k < m && popc(Rset) < rb; ++k) {
                 // fill with tile bits above 0 first (keeps tile bit 0 free for lanes)
                 const int p = (k + 1) % m;
