@@ -247,6 +247,11 @@ void take_pass(const std::vector<PGate> &G, std::vector<int> &pending, uint64_t 
     pending.swap(rest);
 }
 
+int segments_first_fit(const std::vector<PGate> &G, std::vector<int> pending, int rb, uint64_t all);
+
+// Cost of the greedy choice for `pending`: passes, each worth kPassCost
+// segments (an HBM round trip of the state against one shared-memory
+// transposition of it, as measured), plus the segments first fit needs.
 // Passes the greedy choice needs for `pending`.
 int greedy_passes(const std::vector<PGate> &G, std::vector<int> pending, int n, int m, uint64_t lowmask, uint64_t all) {
     int np = 0;
@@ -257,11 +262,32 @@ int greedy_passes(const std::vector<PGate> &G, std::vector<int> pending, int n, 
     return np;
 }
 
+// Rollout objective of the tile lookahead: 0 = passes alone (ties to the
+// greedy choice); c > 0 = c x passes + segments (a pass against the
+// shared-memory transpositions it saves).  plan_tiles plans with both and
+// keeps the plan with fewer passes, then fewer segments: on the measured
+// circuits that is always the faster one, while neither objective alone is.
+thread_local int g_pass_cost = 0;
+int pass_cost() { return g_pass_cost; }
+#define kPassCost pass_cost()
+int greedy_cost(const std::vector<PGate> &G, std::vector<int> pending, int n, int m, int rb, uint64_t lowmask,
+                uint64_t all) {
+    int cost = 0;
+    while (!pending.empty()) {
+        const std::vector<int> before = pending;
+        take_pass(G, pending, choose_tile(G, pending, n, m, lowmask, all), all);
+        std::vector<int> ops;
+        std::set_difference(before.begin(), before.end(), pending.begin(), pending.end(), std::back_inserter(ops));
+        cost += kPassCost + segments_first_fit(G, ops, rb, all);
+    }
+    return cost;
+}
+
 // Tile for the next pass with lookahead: candidates are the greedy choice and
 // the greedy growths started from each of the best single qubits; each is
 // rolled out with the greedy choice to the end, and the one with the fewest
 // passes in total wins (ties: the greedy choice, then more gates now).
-uint64_t choose_tile_lookahead(const std::vector<PGate> &G, const std::vector<int> &pending, int n, int m,
+uint64_t choose_tile_lookahead(const std::vector<PGate> &G, const std::vector<int> &pending, int n, int m, int rb,
                                uint64_t lowmask, uint64_t all, int width) {
     std::vector<uint64_t> cand;
     cand.push_back(choose_tile(G, pending, n, m, lowmask, all));
@@ -290,9 +316,14 @@ uint64_t choose_tile_lookahead(const std::vector<PGate> &G, const std::vector<in
     for (uint64_t T : cand) {
         std::vector<int> rest = pending;
         take_pass(G, rest, T, all);
-        const int np = 1 + greedy_passes(G, rest, n, m, lowmask, all);
+        std::vector<int> ops;
+        std::set_difference(pending.begin(), pending.end(), rest.begin(), rest.end(), std::back_inserter(ops));
+        const int np = kPassCost == 0 ? 1 + greedy_passes(G, rest, n, m, lowmask, all)
+                                      : kPassCost + segments_first_fit(G, ops, rb, all) + greedy_cost(G, rest, n, m, rb, lowmask, all);
         const int cnt = int(pending.size() - rest.size());
-        if (np < best_np || (np == best_np && cnt > best_cnt && T != cand[0] && best != cand[0])) {
+        const bool tie_to_greedy = kPassCost == 0;
+        if (np < best_np || (np == best_np && !tie_to_greedy) ||
+            (np == best_np && cnt > best_cnt && T != cand[0] && best != cand[0])) {
             best_np = np;
             best_cnt = cnt;
             best = T;
@@ -404,7 +435,31 @@ int tile_low64() {
 }
 
 template <typename R>
+sv_status plan_tiles_one(const std::vector<PGate> &G, int n, const TileConfig &cfg, TilePlan<R> *out);
+
+template <typename R>
 sv_status plan_tiles(const std::vector<PGate> &G, int n, const TileConfig &cfg, TilePlan<R> *out) {
+    const char *e = std::getenv("SV_PLAN_PASS_COST");
+    if (e) {  // one objective only
+        g_pass_cost = std::atoi(e);
+        return plan_tiles_one(G, n, cfg, out);
+    }
+    g_pass_cost = 0;
+    sv_status s = plan_tiles_one(G, n, cfg, out);
+    if (s || plan_lookahead_width() == 0) return s;
+    TilePlan<R> alt;
+    g_pass_cost = 4;
+    s = plan_tiles_one(G, n, cfg, &alt);
+    g_pass_cost = 0;
+    if (s) return s;
+    if (alt.passes.size() < out->passes.size() ||
+        (alt.passes.size() == out->passes.size() && alt.segs.size() < out->segs.size()))
+        *out = std::move(alt);
+    return SV_OK;
+}
+
+template <typename R>
+sv_status plan_tiles_one(const std::vector<PGate> &G, int n, const TileConfig &cfg, TilePlan<R> *out) {
     out->passes.clear();
     out->ops.clear();
     out->segs.clear();
@@ -430,7 +485,7 @@ sv_status plan_tiles(const std::vector<PGate> &G, int n, const TileConfig &cfg, 
         // Fewer passes, each fuller: 12 -> 11 passes and 5% less time for
         // the 32-qubit depth-24 circuit, 7 -> 6 for QFT-32.
         const int width = plan_lookahead_width();
-        const uint64_t T = width > 0 ? choose_tile_lookahead(G, pending, n, m, lowmask, all, width)
+        const uint64_t T = width > 0 ? choose_tile_lookahead(G, pending, n, m, rb, lowmask, all, width)
                                      : choose_tile(G, pending, n, m, lowmask, all);
         // ---- collect the pass's gates
         std::vector<int> pass_ops, rest;
