@@ -72,9 +72,11 @@ struct TilePassArgs {
     int op_begin, op_end;
 };
 
-// Register-condition id used by TOP_PHASE / TOP_NEG: mask * 32 + value with
+constexpr int kTileMaxRegs = 64;  // register amplitudes per thread (2^rb, rb <= 6)
+
+// Register-condition id used by TOP_PHASE / TOP_NEG: mask * kTileMaxRegs + value with
 // at most two mask bits.
-constexpr int reg_cond_id(uint32_t mask, uint32_t val) { return int(mask * 32 + val); }
+constexpr int reg_cond_id(uint32_t mask, uint32_t val) { return int(mask * kTileMaxRegs + val); }
 
 struct TileConfig {
     int m;      // tile bits

@@ -171,7 +171,7 @@ std::string gen_pass(const TilePlan<R> &tp, size_t pass) {
     (void)0;
 
     int cur_seg = -1;
-    uint32_t pv[32] = {0};
+    uint32_t pv[kTileMaxRegs] = {0};
     // The stored value of register v is the amplitude divided by
     //   sgn[v] * prod(rsg[v]) * 2^(-me[v] / 2):
     // sgn: compile-time sign (unconditional sign flips such as CZ only flip
@@ -190,9 +190,9 @@ std::string gen_pass(const TilePlan<R> &tp, size_t pass) {
     //   complex factor per distinct list (the running product of
     //   cond ? phase : 1), paid once per register when the register meets
     //   a register with another list, or at the scatter.
-    int sgn[32], me[32];
-    for (int v = 0; v < 32; ++v) sgn[v] = 1, me[v] = 0;
-    std::vector<int> rsg[32], rph[32];
+    int sgn[kTileMaxRegs], me[kTileMaxRegs];
+    for (int v = 0; v < kTileMaxRegs; ++v) sgn[v] = 1, me[v] = 0;
+    std::vector<int> rsg[kTileMaxRegs], rph[kTileMaxRegs];
     std::map<std::vector<int>, std::pair<std::string, std::string>> cph;  // list -> running product (re, im)
     std::map<std::pair<std::vector<int>, std::string>, std::pair<std::string, std::string>> kph;  // times a real factor
     int cph_id = 0;
@@ -344,7 +344,7 @@ std::string gen_pass(const TilePlan<R> &tp, size_t pass) {
             continue;
         }
         if (op.type == TOP_PHASE || op.type == TOP_NEG) {
-            const uint32_t M = uint32_t(op.a) / 32, V = uint32_t(op.a) % 32;
+            const uint32_t M = uint32_t(op.a) / kTileMaxRegs, V = uint32_t(op.a) % kTileMaxRegs;
             const std::string pr = lit(op.u[0]), pi = lit(op.u[1]);
             // (+-1 +- i) / sqrt(2): two additions, the magnitude is owed
             const double ar = std::fabs(double(op.u[0])), ai = std::fabs(double(op.u[1]));
@@ -677,8 +677,8 @@ sv_status jit_compile_check(const TilePlan<float> &tp) { return compile_check_im
 sv_status jit_compile_check(const TilePlan<double> &tp) { return compile_check_impl(tp); }
 
 const char *tile_kernel_name(const sv_state *h) {
-    static const char *n64[] = {"svp<f32,13,4>", "svp<f32,13,5>"};
-    return h->dt == SV_C64 ? n64[tile_rb64() == 5] : "svp<f64,12,4>";
+    static const char *n64[] = {"svp<f32,13,4>", "svp<f32,13,5>", "svp<f32,13,6>"};
+    return h->dt == SV_C64 ? n64[tile_rb64() - 4] : "svp<f64,12,4>";
 }
 
 cudaError_t launch_jit_pass(sv_state *h, void *fn, int n, int rb) {

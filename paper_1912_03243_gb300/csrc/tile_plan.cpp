@@ -420,7 +420,7 @@ int seg_lookahead_width() {
 int tile_rb64() {
     const char *e = std::getenv("SV_TILE_RB");
     const int v = e ? std::atoi(e) : kTileRB64;
-    return (v == 4 || v == 5) ? v : kTileRB64;
+    return (v >= 4 && v <= 6) ? v : kTileRB64;
 }
 
 int plan_lookahead_width() {
