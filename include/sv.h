@@ -126,7 +126,7 @@ sv_status sv_apply_gate(sv_handle h, int target, int control, const double *U);
 
 /* Sec. 2: a k-qubit gate as a dense 2^k x 2^k matrix on the listed qubits
  * (local index bit j <-> qubits[j]; qubits[0] is the least significant).
- * 1 <= k <= 6, qubits distinct.  SV_C64 states of n >= 13 apply it on the
+ * 1 <= k <= 6, qubits distinct.  SV_C64 states of n >= 12 apply it on the
  * tensor cores (tcgen05) with split-precision BF16 products (A_hi B_hi +
  * A_hi B_lo + A_lo B_hi) and FP32 accumulation; smaller SV_C64 states in
  * FP32 and SV_C128 in FP64 on the CUDA cores.  The tensor-core kernel's only

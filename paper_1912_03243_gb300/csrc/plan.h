@@ -13,8 +13,8 @@ constexpr int kMaxFusedQubits = 6;
 
 // Dense k-qubit block (sv_apply_fused); U is 2^k x 2^k complex row-major on
 // the host, copied into handle scratch before the launch.  complex64 states
-// of at least one 2^13 tile run on the tensor cores (launch_fused_tc), the
-// rest on the CUDA cores.
+// of at least one tensor-core tile (2^12 amplitudes) run on the tensor cores
+// (launch_fused_tc), the rest on the CUDA cores.
 cudaError_t launch_fused(sv_state *h, int k, const int *qubits, const double *U);
 bool fused_tc_supported(const sv_state *h);
 cudaError_t launch_fused_tc(sv_state *h, int k, const int *qubits, const double *U);

@@ -1,5 +1,5 @@
 // Tiled multi-gate passes: data structures shared by the host planner
-// (tile_plan.cpp) and the kernel (k_tile.cu).
+// (tile_plan.cpp) and the pass code generator (tile_jit.cpp).
 //
 // A pass picks m "tile" qubits.  Each CTA owns one tile: the 2^m amplitudes
 // whose other (outer) index bits equal the CTA's number, i.e. 2^(m-L) runs
