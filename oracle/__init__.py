@@ -69,6 +69,9 @@ def lib() -> ctypes.CDLL:
                                              ctypes.c_int64, u64p, dp, ip]
             L.orc_cut_amplitudes_part.argtypes = [ctypes.c_char_p, ctypes.c_int, ctypes.c_uint64, ctypes.c_int,
                                                   ctypes.c_uint64, ctypes.c_int, ctypes.c_int64, u64p, dp, ip]
+            L.orc_cut_amplitudes_multi.argtypes = [ctypes.c_char_p, ctypes.c_int, ctypes.POINTER(ctypes.c_ubyte),
+                                                   ctypes.c_int, ctypes.c_int, ctypes.c_uint64, ctypes.c_int,
+                                                   ctypes.c_int64, u64p, ctypes.c_int, dp, ip]
             _lib = L
     return _lib
 
@@ -246,6 +249,36 @@ def cut_amplitudes_part(circuit, mask_a: int, z, part: int, nparts_log2: int, fo
     _check(lib().orc_cut_amplitudes_part(_text(circuit), n, ctypes.c_uint64(mask_a), form, ctypes.c_uint64(part),
                                          nparts_log2, zz.size, zz.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
                                          _dp(out), ctypes.byref(s)))
+    return out.view(np.complex128).copy(), s.value
+
+
+def bit_words(idx, n: int) -> np.ndarray:
+    """Python-int bit strings -> (m, ceil(n/64)) little-endian uint64 words."""
+    nw = (n + 63) // 64
+    out = np.zeros((len(idx), nw), dtype=np.uint64)
+    for j, v in enumerate(idx):
+        v = int(v)
+        for w in range(nw):
+            out[j, w] = (v >> (64 * w)) & ((1 << 64) - 1)
+    return out
+
+
+def cut_amplitudes_multi(circuit, part_of, z, form: int = 0, part: int = 0, nparts_log2: int = 0,
+                         n: int | None = None):
+    """Eq. 3 over P partitions (part_of[q] = partition of qubit q); z: Python
+    ints or (m, ceil(n/64)) uint64 words.  Returns (amplitudes, S)."""
+    if n is None:
+        n = circuit.n
+    po = np.ascontiguousarray(part_of, dtype=np.uint8)
+    z = np.asarray(z)
+    zz = np.ascontiguousarray(z if z.dtype == np.uint64 and z.ndim == 2 else bit_words(list(z), n), dtype=np.uint64)
+    m = zz.shape[0]
+    out = np.zeros(2 * m, dtype=np.float64)
+    s = ctypes.c_int(0)
+    _check(lib().orc_cut_amplitudes_multi(_text(circuit), n, po.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)),
+                                          int(po.max()) + 1, form, ctypes.c_uint64(part), nparts_log2, m,
+                                          zz.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), zz.shape[1], _dp(out),
+                                          ctypes.byref(s)))
     return out.view(np.complex128).copy(), s.value
 
 

@@ -38,6 +38,7 @@
  *                               s is simulated as two independent smaller
  *                               state vectors and <z|C|0> is the sum over s of
  *                               the products of their coefficients.
+ *   orc_cut_amplitudes_multi    the same over P partitions (Sec. 4).
  *
  * Qubit j is bit j of the amplitude index (the paper leaves the order open).
  */
@@ -655,5 +656,118 @@ static int cut_amplitudes_range(const char *text, int n, uint64_t maskA, int for
 done:
     free(psi[0]); free(psi[1]); free(zh[0]); free(zh[1]); free(acc);
     free(prog[0].v); free(prog[1].v);
+    return rc;
+}
+
+
+/* <z|C|0> over P partitions (Sec. 4: the sum over s of products of P
+ * circuits that each act on one partition).  part_of[q] is the partition of
+ * qubit q; every CZ, CP or CX between two partitions is decomposed as in
+ * orc_cut_amplitudes, the projector (or first Eq. 2 factor) on the
+ * partition of the gate's first qubit.  Each term s is simulated as P
+ * independent state vectors and the products of their coefficients are
+ * summed (terms s = part mod 2^nparts_log2 only).  z: m bit strings of
+ * nwords 64-bit words (qubit q is bit q % 64 of word q / 64). */
+int orc_cut_amplitudes_multi(const char *text, int n, const unsigned char *part_of, int P, int form, uint64_t part,
+                             int nparts_log2, int64_t m, const uint64_t *z, int nwords, double *out, int *n_cut_out) {
+    enum { MAXP = 16, MAXQ = 128 };
+    if (form != 0 && form != 1) return ORC_ERR_ARG;
+    if (n < 2 || n > MAXQ || P < 2 || P > MAXP || nwords != (n + 63) / 64) return ORC_ERR_ARG;
+    if (nparts_log2 < 0 || nparts_log2 > 20 || (part >> nparts_log2)) return ORC_ERR_ARG;
+    int loc[MAXQ], side[MAXQ], np[MAXP] = {0};
+    for (int q = 0; q < n; q++) {
+        if (part_of[q] >= P) return ORC_ERR_ARG;
+        side[q] = part_of[q];
+        loc[q] = np[side[q]]++;
+    }
+    for (int p = 0; p < P; p++)
+        if (np[p] == 0 || np[p] > 24) { snprintf(orc_err, sizeof orc_err, "partition %d has %d qubits", p, np[p]); return ORC_ERR_ARG; }
+    orc_circuit c;
+    int rc = parse_circuit(text, n, &c);
+    if (rc) return rc;
+    half_prog prog[MAXP];
+    memset(prog, 0, sizeof prog);
+    int S = 0;
+    for (int g = 0; g < c.count && rc == ORC_OK; g++) {
+        orc_instr *in = &c.v[g];
+        orc_gate gate;
+        instr_gate(in, &gate);
+        if (in->nq == 1 || side[in->q[0]] == side[in->q[1]]) {
+            half_op op; memset(&op, 0, sizeof op);
+            op.kind = 0; op.g = gate;
+            for (int k = 0; k < gate.nq; k++) op.g.q[k] = loc[in->q[k]];
+            rc = prog_push(&prog[side[in->q[0]]], op);
+            continue;
+        }
+        int a = in->q[0], b = in->q[1];
+        double theta;
+        int hq = -1;
+        if (!strcmp(in->name, "CZ")) theta = M_PI;
+        else if (!strcmp(in->name, "CP")) theta = in->p[0];
+        else if (!strcmp(in->name, "CX")) { theta = M_PI; hq = b; }
+        else { rc = ORC_ERR_UNSUPPORTED; snprintf(orc_err, sizeof orc_err, "cannot decompose %s across partitions", in->name); break; }
+        if (form == 1 && fabs(theta - M_PI) > 0) { rc = ORC_ERR_UNSUPPORTED; snprintf(orc_err, sizeof orc_err, "Eq. 2 form decomposes CZ only"); break; }
+        if (S >= 20) { rc = ORC_ERR_UNSUPPORTED; snprintf(orc_err, sizeof orc_err, "too many decomposed gates"); break; }
+        half_op h; memset(&h, 0, sizeof h);
+        if (hq >= 0) {
+            h.kind = 0; h.g.nq = 1; h.g.q[0] = loc[hq];
+            one_qubit_matrix("H", NULL, 0, h.g.m);
+            rc = prog_push(&prog[side[hq]], h);
+            if (rc) break;
+        }
+        half_op opA; memset(&opA, 0, sizeof opA);
+        opA.kind = 1; opA.q = loc[a]; opA.cut = S; opA.role = 0; opA.theta = theta;
+        half_op opB = opA; opB.q = loc[b]; opB.role = 1;
+        rc = prog_push(&prog[side[a]], opA);
+        if (!rc) rc = prog_push(&prog[side[b]], opB);
+        if (!rc && hq >= 0) rc = prog_push(&prog[side[hq]], h);
+        S++;
+    }
+    circuit_free(&c);
+    cplx *psi[MAXP] = {0};
+    uint64_t *zp[MAXP] = {0};
+    cplx *acc = NULL;
+    if (rc) goto done;
+    if (n_cut_out) *n_cut_out = S;
+    for (int p = 0; p < P; p++) {
+        psi[p] = malloc(((uint64_t)1 << np[p]) * sizeof(cplx));
+        zp[p] = malloc((size_t)(m > 0 ? m : 1) * sizeof(uint64_t));
+        if (!psi[p] || !zp[p]) { rc = ORC_ERR_MEM; goto done; }
+    }
+    acc = calloc((size_t)(m > 0 ? m : 1), sizeof(cplx));
+    if (!acc) { rc = ORC_ERR_MEM; goto done; }
+    for (int64_t j = 0; j < m; j++) {  /* each z split into its partitions' indices */
+        for (int p = 0; p < P; p++) zp[p][j] = 0;
+        for (int q = 0; q < n; q++) {
+            uint64_t bitv = (z[j * nwords + q / 64] >> (q % 64)) & 1;
+            zp[side[q]][j] |= bitv << loc[q];
+        }
+    }
+    double w = form == 1 ? ldexp(1.0, -S) : 1.0;
+    for (uint64_t s = part; s < ((uint64_t)1 << S); s += (uint64_t)1 << nparts_log2) {
+        for (int p = 0; p < P; p++) {
+            uint64_t dim = (uint64_t)1 << np[p];
+            memset(psi[p], 0, dim * sizeof(cplx));
+            psi[p][0] = 1;
+            for (int k = 0; k < prog[p].count; k++) {
+                half_op *op = &prog[p].v[k];
+                if (op->kind == 0) apply_gate(psi[p], np[p], &op->g);
+                else {
+                    cplx d[2];
+                    branch_diag(form, op->role, (int)((s >> op->cut) & 1), op->theta, d);
+                    apply_diag1(psi[p], np[p], op->q, d);
+                }
+            }
+        }
+        for (int64_t j = 0; j < m; j++) {
+            cplx t = w;
+            for (int p = 0; p < P; p++) t *= psi[p][zp[p][j]];
+            acc[j] += t;
+        }
+    }
+    for (int64_t j = 0; j < m; j++) { out[2 * j] = creal(acc[j]); out[2 * j + 1] = cimag(acc[j]); }
+done:
+    for (int p = 0; p < P; p++) { free(psi[p]); free(zp[p]); free(prog[p].v); }
+    free(acc);
     return rc;
 }

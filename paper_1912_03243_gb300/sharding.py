@@ -51,3 +51,14 @@ def cut_amplitudes_sharded(circuit, n: int, mask_a: int, z, form: int = 0, group
     zz = np.ascontiguousarray(z, dtype=np.uint64)
     return sharded_sum(lambda part, p: sv.sv_cut_amplitudes_part(circuit, n, mask_a, zz, part, p, form)[0], zz.size,
                        group)
+
+
+def cut_amplitudes_multi_sharded(circuit, n: int, part_of, z_words, form: int = 0, group=None) -> np.ndarray:
+    """The same over P partitions (z_words: (m, ceil(n/64)) uint64 bit
+    strings)."""
+    from paper_1912_03243_gb300 import sv
+
+    zz = np.ascontiguousarray(z_words, dtype=np.uint64).reshape(-1, (n + 63) // 64)
+    return sharded_sum(
+        lambda part, p: sv.sv_cut_amplitudes_multi(circuit, n, part_of, zz, form, part=part, nparts_log2=p)[0],
+        zz.shape[0], group)

@@ -46,3 +46,19 @@ def bench_max(rank, world, port, out_path):
         with open(out_path, "w") as f:
             json.dump({"max": v}, f)
     dist.destroy_process_group()
+
+
+def sharded_oracle_multi_sum(rank, world, port, circuit_text, n, part_of, z, out_path):
+    import numpy as np
+
+    import oracle
+    from paper_1912_03243_gb300 import sharding
+
+    dist = _init(rank, world, port)
+    total = sharding.sharded_sum(
+        lambda part, p: oracle.cut_amplitudes_multi(circuit_text, part_of, z, part=part, nparts_log2=p, n=n)[0],
+        len(z))
+    if rank == 0:
+        np.save(out_path, total)
+    dist.barrier()
+    dist.destroy_process_group()

@@ -105,3 +105,17 @@ def test_errors(S):
         sw = C.Circuit(8)
         sw.add("SWAP", 0, 7)
         S.sv_cut_amplitudes_multi(sw, 8, [q // 4 for q in range(8)], z)
+
+
+@pytest.mark.parametrize("form", [0, 1])
+def test_30q_three_partitions_vs_oracle(S, orc, form):
+    """Beyond the full state's reach in the oracle: a 6x5 grid (30 qubits),
+    depth 8, in three partitions of two rows (10 decomposed CZs), 256 seeded
+    amplitudes against the oracle's own P-partition sum."""
+    c = C.grid_circuit(6, 5, 8, 4)
+    part_of = [(q // 5) // 2 for q in range(30)]
+    idx = [int(v) for v in C.random_bitstrings(256, 30, 9)]
+    got, s = S.sv_cut_amplitudes_multi(c, 30, part_of, words(idx, 30), form=form)
+    ref, s_ref = orc.cut_amplitudes_multi(c, part_of, idx, form=form)
+    assert s == s_ref == 10
+    close(got, ref)

@@ -97,3 +97,17 @@ def test_bench_reference_arm_two_ranks():
     assert len(lines) == 1
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["unit"] == "gates/s" and d["value"] > 0
+
+
+def test_sharded_multi_partition_sum_gloo(orc, tmp_path):
+    """Branch parts of the P-partition sum (4 partitions) over 2 gloo ranks
+    equal the unsharded oracle sum."""
+    import mp_helpers
+
+    c = C.grid_circuit(4, 3, 8, 7)
+    part_of = [q // 3 for q in range(12)]
+    z = list(range(0, 1 << 12, 3))
+    out = tmp_path / "multi.npy"
+    spawn(mp_helpers.sharded_oracle_multi_sum, 2, c.text(), c.n, part_of, z, str(out))
+    full, _ = orc.cut_amplitudes_multi(c, part_of, z)
+    assert np.max(np.abs(np.load(out) - full)) < 1e-12

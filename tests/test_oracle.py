@@ -407,3 +407,42 @@ def test_codec_fidelity_random_circuit(orc):
     got = orc.enc_decode(codes, scales).astype(np.complex128)
     f = abs(np.vdot(exact, got)) ** 2 / (orc.norm(exact) * orc.norm(got))
     assert f > 0.995, f
+
+
+# --------------------------------------------- P-partition decomposition
+
+@pytest.mark.parametrize("form", [0, 1])
+@pytest.mark.parametrize("rows,cols,depth,P", [(4, 3, 8, 4), (3, 4, 9, 3), (4, 3, 10, 2)])
+def test_cut_multi_equals_full_state(orc, form, rows, cols, depth, P):
+    """Sec. 4 over P partitions (row bands of a grid): every amplitude equals
+    the full-state simulation, the plain definition of <z|C|0>."""
+    c = C.grid_circuit(rows, cols, depth, 3)
+    n = c.n
+    band = -(-rows // P)
+    part_of = [min((q // cols) // band, P - 1) for q in range(n)]
+    amps, s = orc.cut_amplitudes_multi(c, part_of, list(range(1 << n)), form=form)
+    assert s > 0
+    assert np.max(np.abs(amps - orc.run(c))) < 1e-12
+
+
+def test_cut_multi_parts_add_up(orc):
+    c = C.grid_circuit(4, 3, 8, 5)
+    part_of = [q // 3 for q in range(12)]
+    z = list(range(1 << 12))
+    full, s = orc.cut_amplitudes_multi(c, part_of, z)
+    acc = sum(orc.cut_amplitudes_multi(c, part_of, z, part=p, nparts_log2=2)[0] for p in range(4))
+    assert np.max(np.abs(acc - full)) < 1e-12
+
+
+def test_cut_multi_ghz_128(orc):
+    """Sec. 4: the 128-qubit GHZ chain in 8 partitions of 16 qubits (7 cut
+    CNOTs, bit strings of two 64-bit words): <0...0|C|0> = <1...1|C|0> =
+    1/sqrt(2), other coefficients 0."""
+    n = 128
+    c = C.ghz_circuit(n)
+    idx = [0, (1 << n) - 1, 1, 1 << 64, (1 << 127) | 5, (1 << 64) - 1]
+    for form in (0, 1):
+        amps, s = orc.cut_amplitudes_multi(c, [q // 16 for q in range(n)], idx, form=form)
+        assert s == 7
+        assert np.allclose(amps[:2], 1 / math.sqrt(2), atol=1e-14)
+        assert np.max(np.abs(amps[2:])) < 1e-14
