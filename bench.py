@@ -461,7 +461,9 @@ def bench_30q(S, C, hbm_peak):
 def bench_expect(S, C, hbm_peak):
     """<sigma^alpha_i> for all 32 qubits and alpha = x, y, z of the 32-qubit
     uniform superposition (Sec. 3 validation observable): read-only passes
-    over the 32 GiB state (1 + ceil((32 - 13) / 9) = 4)."""
+    over the 32 GiB state, 2^13-amplitude tiles of which the later passes
+    share SV_EXPECT_LOW (default 3) low qubits with the first:
+    1 + ceil((32 - 13) / (13 - 3)) = 3."""
     import numpy as np
     import torch
 
@@ -475,7 +477,8 @@ def bench_expect(S, C, hbm_peak):
     for _ in range(reps):
         sig = st.expect_pauli()
     t = (time.perf_counter() - t0) / reps
-    passes = 1 + -(-(n - 13) // 9)
+    low = max(3, min(8, int(os.environ.get("SV_EXPECT_LOW", "3"))))
+    passes = 1 + -(-(n - 13) // (13 - low))
     q = (1 - sig / st.norm()) / 2
     st.free()
     del st

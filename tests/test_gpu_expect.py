@@ -35,8 +35,8 @@ def oracle_expect(orc, psi):
 @pytest.mark.parametrize("n", [1, 3, 12, 13, 17, 22])
 def test_random_states(S, orc, dtype, tol, n):
     """n = 1..12 fit one tile; 13 is one tile of 2^13 (complex64) or two
-    (complex128); 17 and 22 need several passes (tiles keep the low 4
-    qubits and take up to 9 uncovered ones)."""
+    (complex128); 17 and 22 need several passes (complex64 tiles keep the low
+    3 qubits and take up to 10 uncovered ones)."""
     psi = C.random_state(n, 40 + n)
     s = S.StateVector(n, dtype)
     s.from_numpy(psi)
@@ -44,6 +44,21 @@ def test_random_states(S, orc, dtype, tol, n):
     ref = oracle_expect(orc, s.to_numpy().astype(np.complex128))
     assert got.shape == (n, 3)
     assert np.max(np.abs(got - ref)) <= tol
+
+
+@pytest.mark.parametrize("low", ["4", "5", "8"])
+def test_low_qubit_variants(S, orc, monkeypatch, low):
+    """Later passes that keep 4, 5 or 8 low qubits (SV_EXPECT_LOW) instead of
+    3: more passes, uncovered qubits in other tile bits, covered ones as
+    fillers; the same values."""
+    monkeypatch.setenv("SV_EXPECT_LOW", low)
+    n = 21
+    psi = C.random_state(n, 77)
+    s = S.StateVector(n, "c64")
+    s.from_numpy(psi)
+    got = s.expect_pauli()
+    ref = oracle_expect(orc, s.to_numpy().astype(np.complex128))
+    assert np.max(np.abs(got - ref)) <= 2e-6
 
 
 @pytest.mark.parametrize("n", [5, 8, 12, 16, 21])
