@@ -158,6 +158,18 @@ def test_register_budget_variants(S, orc, monkeypatch, ctas):
     check("c64", s.to_numpy(), orc.run(c))
 
 
+@pytest.mark.parametrize("rb", ["4", "6"])
+def test_register_qubit_variants(S, orc, monkeypatch, rb):
+    """Passes generated for 4 or 6 register qubits per thread (SV_TILE_RB:
+    512- or 128-thread CTAs, other register sets and segment boundaries) give
+    the same states as the default of 5."""
+    monkeypatch.setenv("SV_TILE_RB", rb)
+    c = C.random_circuit(21, 10, 13)
+    s = S.StateVector(21, "c64")
+    s.run(c, "tiled")
+    check("c64", s.to_numpy(), orc.run(c))
+
+
 def test_plan_cache_reuse(S, orc):
     """Tiled plans are cached by circuit text (with the device, dtype, qubit
     count and planner settings in the key): running the same text again on a
