@@ -42,6 +42,14 @@ __device__ __forceinline__ uint64_t insert_zero(uint64_t x, int p) {
     return ((x ^ lo) << 1) | lo;
 }
 
+// Zero bits inserted at the ascending positions p0, p1 (the first nins of
+// them); constant indices keep the launch arguments out of local memory.
+__device__ __forceinline__ uint64_t insert_zeros(uint64_t x, int nins, int p0, int p1) {
+    if (nins > 0) x = insert_zero(x, p0);
+    if (nins > 1) x = insert_zero(x, p1);
+    return x;
+}
+
 // Signed table, indexed by the code's byte u = (uint8)q: tab[u * 32 + lane] =
 // sign(q) fl(|q| / 127), replicated per bank.  fl(s * (-t)) = -fl(s * t), so
 // s * tab[u] is exactly sign(q) fl(s T[|q|]).
@@ -63,6 +71,16 @@ __device__ __forceinline__ float dec1(uint32_t u, float s, const float *tab, int
 // rint(x * fl(127/s)).  No clamp is needed: s is the exact maximum of |x| over
 // the block, so |x * fl(127/s)| <= 127 (1 + 2^-24)^2 < 127.5.
 __device__ __forceinline__ int enc1(float x, float inv) { return __float2int_rn(__fmul_rn(x, inv)); }
+
+// The same code as a byte, without a float-to-integer conversion: for
+// |v| < 2^22 the sum v + 1.5 * 2^23 lies in [2^23, 2^24), where the float
+// spacing is 1, so the (round-to-nearest-even) addition yields exactly
+// rint(v) + 1.5 * 2^23, whose bit pattern is 0x4B400000 + rint(v).  Its low
+// byte is rint(v) mod 256, the two's-complement code byte.  The product is
+// rounded on its own first (no contraction), as in enc1.
+__device__ __forceinline__ uint32_t enc_bits(float x, float inv) {
+    return __float_as_uint(__fadd_rn(__fmul_rn(x, inv), 12582912.0f));
+}
 
 __device__ __forceinline__ void gate_pair(const float *u, float &ar, float &ai, float &br, float &bi) {
     const float r0 = __fmaf_rn(u[0], ar, __fmaf_rn(-u[1], ai, __fmaf_rn(u[2], br, -__fmul_rn(u[3], bi))));
@@ -119,13 +137,17 @@ struct Lane8 {
     float re[8], im[8];
 };
 
+// Byte k of w, zero-extended (one byte permute).
+__device__ __forceinline__ uint32_t byte_of(uint32_t w, int k) { return __byte_perm(w, 0u, 0x4440u | uint32_t(k)); }
+
 __device__ __forceinline__ void decode_lane(const int4 raw, float s, const float *tab, int lane, Lane8 &x) {
     const uint32_t w[4] = {uint32_t(raw.x), uint32_t(raw.y), uint32_t(raw.z), uint32_t(raw.w)};
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-        const uint32_t word = w[j >> 1], sh = (j & 1) * 16;
-        x.re[j] = dec1((word >> sh) & 0xFFu, s, tab, lane);
-        x.im[j] = dec1((word >> (sh + 8)) & 0xFFu, s, tab, lane);
+        const uint32_t word = w[j >> 1];
+        const int k = (j & 1) * 2;
+        x.re[j] = dec1(byte_of(word, k), s, tab, lane);
+        x.im[j] = dec1(byte_of(word, k + 1), s, tab, lane);
     }
 }
 
@@ -143,10 +165,10 @@ __device__ __forceinline__ int4 encode_lane(const Lane8 &x, float s) {
     uint32_t w[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        const uint32_t b0 = uint32_t(enc1(x.re[2 * k], inv)) & 0xFFu, b1 = uint32_t(enc1(x.im[2 * k], inv)) & 0xFFu;
-        const uint32_t b2 = uint32_t(enc1(x.re[2 * k + 1], inv)) & 0xFFu,
-                       b3 = uint32_t(enc1(x.im[2 * k + 1], inv)) & 0xFFu;
-        w[k] = b0 | (b1 << 8) | (b2 << 16) | (b3 << 24);
+        // low bytes of the four sums: (re, im) of amplitudes 2k and 2k + 1
+        const uint32_t lo = __byte_perm(enc_bits(x.re[2 * k], inv), enc_bits(x.im[2 * k], inv), 0x0040u);
+        const uint32_t hi = __byte_perm(enc_bits(x.re[2 * k + 1], inv), enc_bits(x.im[2 * k + 1], inv), 0x0040u);
+        w[k] = __byte_perm(lo, hi, 0x5410u);
     }
     return make_int4(int(w[0]), int(w[1]), int(w[2]), int(w[3]));
 }
@@ -156,6 +178,18 @@ __device__ __forceinline__ bool ctl_ok(int c, int lane, int j) {
     if (c < 0 || c >= kEncBlockLog2) return true;
     const int idx = lane * 8 + j;
     return (idx >> c) & 1;
+}
+
+// Pairs inside a lane (target bit TB < 8 of the lane's 8 amplitudes); the
+// bit is a compile-time constant so the registers are indexed statically.
+template <int SHAPE, int TB>
+__device__ __forceinline__ void lane_pairs(const EncGateArgs &a, int lane, Lane8 &x) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        if (j & TB) continue;
+        if (!ctl_ok(a.c, lane, j)) continue;
+        gate_pair_s<SHAPE>(a.u, x.re[j], x.im[j], x.re[j | TB], x.im[j | TB]);
+    }
 }
 
 // Target inside the block (t < 8).
@@ -169,20 +203,19 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta) k_enc_gate_in(int4 *__restr
     const uint64_t nw = uint64_t(gridDim.x) * kWarpsPerCta;
     for (uint64_t w = wid; w < a.nwork; w += nw) {
         uint64_t b = w;
-        for (int k = 0; k < a.nins; ++k) b = insert_zero(b, a.ins[k]);
+        b = insert_zeros(b, a.nins, a.ins[0], a.ins[1]);
         b |= a.set_mask;
         int4 raw = codes[b * 32 + lane];
         const float s = scales[b];
         Lane8 x;
         decode_lane(raw, s, tab, lane, x);
         if (a.t < 3) {
-            const int tb = 1 << a.t;
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                if (j & tb) continue;
-                if (!ctl_ok(a.c, lane, j)) continue;
-                gate_pair_s<SHAPE>(a.u, x.re[j], x.im[j], x.re[j | tb], x.im[j | tb]);
-            }
+            if (a.t == 0)
+                lane_pairs<SHAPE, 1>(a, lane, x);
+            else if (a.t == 1)
+                lane_pairs<SHAPE, 2>(a, lane, x);
+            else
+                lane_pairs<SHAPE, 4>(a, lane, x);
         } else {
             const int lb = 1 << (a.t - 3);
             const bool upper = lane & lb;
@@ -215,7 +248,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta) k_enc_gate_across(int4 *__r
     const uint64_t nw = uint64_t(gridDim.x) * kWarpsPerCta;
     for (uint64_t w = wid; w < a.nwork; w += nw) {
         uint64_t b0 = w;
-        for (int k = 0; k < a.nins; ++k) b0 = insert_zero(b0, a.ins[k]);
+        b0 = insert_zeros(b0, a.nins, a.ins[0], a.ins[1]);
         b0 |= a.set_mask;
         const uint64_t b1 = b0 | a.tbit;
         int4 r0 = codes[b0 * 32 + lane], r1 = codes[b1 * 32 + lane];
@@ -236,6 +269,36 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta) k_enc_gate_across(int4 *__r
             scales[b0] = n0;
             scales[b1] = n1;
         }
+    }
+}
+
+// Diagonal gate with u00 = 1 (T, P, ...) on a target at or above bit 8: the
+// blocks with the target bit 0 keep their amplitudes, hence their scale and
+// codes (decoding and re-encoding with an unchanged scale is the identity), so
+// only the blocks with the target bit 1 are read and rewritten: half the
+// traffic of the block-pair kernel, the same codes.
+__global__ void __launch_bounds__(32 * kWarpsPerCta) k_enc_phase_blocks(int4 *__restrict__ codes,
+                                                                        float *__restrict__ scales, EncGateArgs a) {
+    __shared__ float tab[kTabFloats];
+    load_table(tab);
+    const int lane = threadIdx.x & 31;
+    const uint64_t wid = uint64_t(blockIdx.x) * kWarpsPerCta + (threadIdx.x >> 5);
+    const uint64_t nw = uint64_t(gridDim.x) * kWarpsPerCta;
+    for (uint64_t w = wid; w < a.nwork; w += nw) {
+        const uint64_t b = insert_zeros(w, a.nins, a.ins[0], a.ins[1]) | a.set_mask | a.tbit;
+        const int4 raw = codes[b * 32 + lane];
+        const float s = scales[b];
+        Lane8 y;
+        decode_lane(raw, s, tab, lane, y);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            if (!ctl_ok(a.c, lane, j)) continue;
+            float ar = 0.0f, ai = 0.0f;  // the lower amplitude is left out (u00 = 1, u01 = u10 = 0)
+            gate_pair_s<ENC_DIAG1>(a.u, ar, ai, y.re[j], y.im[j]);
+        }
+        const float ns = warp_max(lane_absmax(y));
+        codes[b * 32 + lane] = encode_lane(y, ns);
+        if (lane == 0) scales[b] = ns;
     }
 }
 
@@ -355,7 +418,7 @@ __global__ void __launch_bounds__(256) k_enc_flip(uint4 *__restrict__ codes, Enc
     const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
     for (uint64_t w = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; w < a.nwork; w += stride) {
         uint64_t b = w >> 5;  // selected block number, 32 words per block
-        for (int k = 0; k < a.nins; ++k) b = insert_zero(b, a.ins[k]);
+        b = insert_zeros(b, a.nins, a.ins[0], a.ins[1]);
         b |= a.set_mask;
         const uint32_t lane = uint32_t(w & 31);
         uint4 v = codes[b * 32 + lane];
@@ -382,7 +445,7 @@ __global__ void __launch_bounds__(256) k_enc_xin(uint4 *__restrict__ codes, EncG
     const uint64_t nw = uint64_t(gridDim.x) * 8;
     for (uint64_t w = wid; w < a.nwork; w += nw) {
         uint64_t b = w;
-        for (int k = 0; k < a.nins; ++k) b = insert_zero(b, a.ins[k]);
+        b = insert_zeros(b, a.nins, a.ins[0], a.ins[1]);
         b |= a.set_mask;
         const uint4 v = codes[b * 32 + lane];
         uint4 p;
@@ -423,7 +486,7 @@ __global__ void __launch_bounds__(256) k_enc_xblocks(uint4 *__restrict__ codes, 
     const uint64_t nw = uint64_t(gridDim.x) * 8;
     for (uint64_t w = wid; w < a.nwork; w += nw) {
         uint64_t b0 = w;
-        for (int k = 0; k < a.nins; ++k) b0 = insert_zero(b0, a.ins[k]);
+        b0 = insert_zeros(b0, a.nins, a.ins[0], a.ins[1]);
         b0 |= a.set_mask;
         const uint64_t b1 = b0 | a.tbit;
         const uint4 v0 = codes[b0 * 32 + lane], v1 = codes[b1 * 32 + lane];
@@ -529,7 +592,7 @@ cudaError_t launch_enc_gate1(sv_state *h, const Gate1 &g) {
         switch (shape) {
             case ENC_REAL: k_enc_gate_across<ENC_REAL><<<grid, block, 0, h->stream>>>(codes, h->scales, a); break;
             case ENC_DIAG: k_enc_gate_across<ENC_DIAG><<<grid, block, 0, h->stream>>>(codes, h->scales, a); break;
-            case ENC_DIAG1: k_enc_gate_across<ENC_DIAG1><<<grid, block, 0, h->stream>>>(codes, h->scales, a); break;
+            case ENC_DIAG1: k_enc_phase_blocks<<<grid, block, 0, h->stream>>>(codes, h->scales, a); break;
             default: k_enc_gate_across<ENC_GENERAL><<<grid, block, 0, h->stream>>>(codes, h->scales, a); break;
         }
     }

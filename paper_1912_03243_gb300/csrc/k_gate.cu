@@ -366,7 +366,12 @@ const char *gate1_kernel_name(const sv_state *h, const Gate1 &g) {
                 if (g.control < 0 || g.control >= kEncBlockLog2) return "k_enc_xblocks";
             }
         }
-        return g.target < kEncBlockLog2 || h->n < kEncBlockLog2 ? "k_enc_gate_in" : "k_enc_gate_across";
+        if (g.target < kEncBlockLog2 || h->n < kEncBlockLog2) return "k_enc_gate_in";
+        // diagonal with u00 = 1 in the FP32 entries the kernels use: only the upper blocks
+        auto zero32 = [](const Cplx &z) { return float(z.re) == 0.0f && float(z.im) == 0.0f; };
+        if (zero32(u[1]) && zero32(u[2]) && float(u[0].re) == 1.0f && float(u[0].im) == 0.0f)
+            return "k_enc_phase_blocks";
+        return "k_enc_gate_across";
     }
     const bool diag = g.u[1].re == 0 && g.u[1].im == 0 && g.u[2].re == 0 && g.u[2].im == 0;
     const bool unit00 = g.u[0].re == 1 && g.u[0].im == 0;

@@ -16,6 +16,7 @@ double gate1_bytes(const sv_state *h, const Gate1 &g) {
         int blockbits = 0;
         if (g.control >= kEncBlockLog2) ++blockbits;
         const bool flip = k == "k_enc_flip";
+        if (k == "k_enc_phase_blocks") ++blockbits;  // the blocks with the target bit set
         if (flip) {
             const bool both = g.u[0].re == -1 && g.u[3].re == -1;
             if (!both && g.target >= kEncBlockLog2) ++blockbits;

@@ -70,6 +70,7 @@ def test_gate_every_target_control_bit_exact(S, orc, n):
     rng = np.random.default_rng(n)
     z = rng.normal(size=(2, 2)) + 1j * rng.normal(size=(2, 2))
     mats.append(np.linalg.qr(z)[0])
+    mats.append(np.diag([1.0, np.exp(0.3j)]))  # a phase (u00 = 1) other than T
     for u in mats:
         for t in range(n):
             for c in [-1] + [q for q in range(n) if q != t]:
