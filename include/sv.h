@@ -148,7 +148,17 @@ sv_status sv_run_circuit(sv_handle h, const char *text, int mode);
  * upload the pass programs) and execute it many times.  The plan is bound
  * to the handle and must be freed before it. */
 sv_status sv_plan_create(sv_handle h, const char *text, int mode, sv_plan *out);
+/* Execute a plan on the handle's stream (asynchronous).  The first execution
+ * launches the kernels one by one; the second captures them into a CUDA graph
+ * on a stream the plan owns, and every later one replays that graph; the
+ * plan's stream waits for the handle's stream before the graph and the
+ * handle's stream waits for the graph after it, so the order of work on the
+ * handle's stream is unchanged.  Plans with CUDA-core dense blocks (host
+ * matrix copies per launch), single-launch plans and runs with SV_GRAPH=0
+ * always launch directly; so does a plan whose capture failed. */
 sv_status sv_plan_execute(sv_plan p);
+/* *out = 1 if the plan's executions now replay a CUDA graph, else 0. */
+sv_status sv_plan_uses_graph(sv_plan p, int *out);
 /* Statistics of a plan: number of gates, HBM passes (kernel launches) and
  * the algorithmic bytes all passes move. */
 sv_status sv_plan_info(sv_plan p, int64_t *gates, int64_t *passes, double *bytes);

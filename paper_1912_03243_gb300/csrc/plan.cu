@@ -1,4 +1,5 @@
 // Plan creation and replay.
+#include <cstdlib>
 #include <string>
 
 #include <mutex>
@@ -36,6 +37,10 @@ double gate1_bytes(const sv_state *h, const Gate1 &g) {
 namespace {
 
 void destroy_plan(sv_plan_s *p) {
+    if (p->gexec) cudaGraphExecDestroy(p->gexec);
+    for (cudaEvent_t e : p->gev)
+        if (e) cudaEventDestroy(e);
+    if (p->gstream) cudaStreamDestroy(p->gstream);
     if (p->d_tcA) cudaFree(p->d_tcA);
     delete p;
 }
@@ -230,15 +235,97 @@ sv_status sv_plan_create(sv_handle h, const char *text, int mode, sv_plan *out) 
     return SV_OK;
 }
 
+namespace sv {
+namespace {
+
+sv_status execute_direct(sv_plan_s *p) {
+    for (const PlanLaunch &l : p->launches) {
+        sv_status s = check_launch(launch_one(p, l), "sv_plan_execute");
+        if (s) return s;
+    }
+    return SV_OK;
+}
+
+// Graph replay applies to plans of two or more launches that are kernel
+// launches only (the CUDA-core dense blocks copy their matrix from host
+// memory at launch time), unless SV_GRAPH=0 or a host-side fault injection
+// is active (it acts per launch).
+bool graph_wanted(const sv_plan_s *p) {
+    if (p->graph_off || p->launches.size() < 2) return false;
+    const char *g = std::getenv("SV_GRAPH");
+    if (g && g[0] == '0') return false;
+    if (std::getenv("SV_FAULT_INJECT")) return false;
+    for (const PlanLaunch &l : p->launches)
+        if (l.kind == 3) return false;
+    return true;
+}
+
+// Capture the launches on the private stream (thread-local mode: a call that
+// is not allowed during capture fails instead of running) and instantiate.
+cudaError_t capture_graph(sv_plan_s *p) {
+    sv_state *h = p->h;
+    cudaError_t e = cudaSuccess;
+    if (!p->gstream) e = cudaStreamCreateWithFlags(&p->gstream, cudaStreamNonBlocking);
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i)
+        if (!p->gev[i]) e = cudaEventCreateWithFlags(&p->gev[i], cudaEventDisableTiming);
+    if (e != cudaSuccess) return e;
+    const cudaStream_t user = h->stream;
+    h->stream = p->gstream;  // the launch functions launch on the handle's stream
+    e = cudaStreamBeginCapture(p->gstream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaError_t le = cudaSuccess;
+        for (const PlanLaunch &l : p->launches) {
+            le = launch_one(p, l);
+            if (le != cudaSuccess) break;
+        }
+        cudaGraph_t g = nullptr;
+        const cudaError_t ee = cudaStreamEndCapture(p->gstream, &g);
+        e = le != cudaSuccess ? le : ee;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&p->gexec, g, 0ULL);
+        if (g) cudaGraphDestroy(g);
+    }
+    h->stream = user;
+    if (e != cudaSuccess) {
+        if (p->gexec) cudaGraphExecDestroy(p->gexec);
+        p->gexec = nullptr;
+    }
+    return e;
+}
+
+sv_status execute_graph(sv_plan_s *p) {
+    sv_state *h = p->h;
+    SV_CUDA_TRY(cudaEventRecord(p->gev[0], h->stream));
+    SV_CUDA_TRY(cudaStreamWaitEvent(p->gstream, p->gev[0], 0));
+    SV_CUDA_TRY(cudaGraphLaunch(p->gexec, p->gstream));
+    SV_CUDA_TRY(cudaEventRecord(p->gev[1], p->gstream));
+    SV_CUDA_TRY(cudaStreamWaitEvent(h->stream, p->gev[1], 0));
+    return SV_OK;
+}
+
+}  // namespace
+}  // namespace sv
+
 sv_status sv_plan_execute(sv_plan p) {
     if (!p) {
         set_error("NULL plan");
         return SV_ERR_ARG;
     }
-    for (const PlanLaunch &l : p->launches) {
-        sv_status s = check_launch(launch_one(p, l), "sv_plan_execute");
-        if (s) return s;
+    if (!graph_wanted(p) || p->execs++ == 0) return execute_direct(p);
+    if (!p->gexec && capture_graph(p) != cudaSuccess) {
+        // not capturable here: clear the error state and launch directly from now on
+        cudaGetLastError();
+        p->graph_off = true;
+        return execute_direct(p);
     }
+    return execute_graph(p);
+}
+
+sv_status sv_plan_uses_graph(sv_plan p, int *out) {
+    if (!p || !out) {
+        set_error("NULL argument");
+        return SV_ERR_ARG;
+    }
+    *out = p->gexec != nullptr ? 1 : 0;
     return SV_OK;
 }
 

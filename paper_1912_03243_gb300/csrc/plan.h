@@ -62,4 +62,14 @@ struct sv_plan_s {
     int fused_k = 0;
     std::vector<PlanLaunch> launches;      // execution order
     double bytes = 0.0;                    // algorithmic bytes of one execution
+    // CUDA graph of the launches, from the second execution on: captured on a
+    // private stream that joins the handle's stream through two events (the
+    // handle's stream may be the legacy default stream, which cannot be
+    // captured).  The first execution runs the launches directly and does the
+    // one-time set-up they need (error word, kernel attributes).
+    int64_t execs = 0;
+    bool graph_off = false;                // capture failed or not applicable: direct launches
+    cudaStream_t gstream = nullptr;
+    cudaEvent_t gev[2] = {nullptr, nullptr};
+    cudaGraphExec_t gexec = nullptr;
 };

@@ -49,6 +49,7 @@ SIGNATURES = {
     "sv_plan_create": (_st, [_vp, ctypes.c_char_p, ctypes.c_int, ctypes.POINTER(_vp)]),
     "sv_plan_execute": (_st, [_vp]),
     "sv_plan_info": (_st, [_vp, _i64p, _i64p, _dp]),
+    "sv_plan_uses_graph": (_st, [_vp, ctypes.POINTER(ctypes.c_int)]),
     "sv_plan_execute_timed": (_st, [_vp, ctypes.POINTER(_vp), ctypes.c_int64]),
     "sv_plan_free": (_st, [_vp]),
     "sv_plan_stats": (_st, [ctypes.c_char_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, _i64p, _i64p, _i64p]),
@@ -214,6 +215,12 @@ class Plan:
 
     def execute(self) -> None:
         _check(lib().sv_plan_execute(self.handle), "sv_plan_execute")
+
+    def uses_graph(self) -> bool:
+        """True once executions replay a CUDA graph (from the second one on)."""
+        v = ctypes.c_int()
+        _check(lib().sv_plan_uses_graph(self.handle, ctypes.byref(v)), "sv_plan_uses_graph")
+        return bool(v.value)
 
     def execute_timed(self, events) -> None:
         """events: list of torch.cuda.Event (passes + 1), recorded around each launch."""
