@@ -99,3 +99,16 @@ def test_tiled_plans_compile_for_sm103a(L):
     assert g == 1140 and p <= 30
     with pytest.raises(sv.SVError):
         sv.sv_plan_stats(C.random_circuit(8, 2, 1), 8, "c64")
+
+
+@pytest.mark.parametrize("name,n,gates,passes,segments", [("random", 32, 1140, 11, 32), ("random", 28, 996, 9, 30),
+                                                         ("random", 30, 712, 8, 23), ("qft", 32, 564, 6, 17)])
+def test_planner_does_not_regress(L, name, n, gates, passes, segments):
+    """Upper bounds on HBM passes and shared-memory transpositions of the
+    benchmark circuits (each pass moves the whole state twice; each segment
+    transposes a tile through shared memory): the planner's lookahead plans
+    (complex64, 2^13-amplitude tiles, 5 register qubits per thread)."""
+    c = C.random_circuit(n, {32: 24, 28: 24, 30: 16}[n], 1) if name == "random" else C.qft_circuit(n, 0x9E3779B9)
+    g, p, s = sv.sv_plan_stats(c, n, "c64")
+    assert g == gates
+    assert p <= passes and s <= segments, (p, s)
