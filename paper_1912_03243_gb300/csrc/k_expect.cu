@@ -559,8 +559,8 @@ extern "C" sv_status sv_expect_pauli(sv_handle h, double *out) {
     const size_t elem = h->dt == SV_C128 ? 16 : 8;
     const size_t smem = (size_t(1) << m) * elem;
     {
-        static bool configured = false;
-        if (!configured) {
+        static std::atomic<uint64_t> configured{0};
+        if (attrs_needed(configured, h->device)) {
             const int big = (1 << kExMaxM) * 8;  // the largest tile: 64 KiB
             SV_CUDA_TRY(cudaFuncSetAttribute(k_expect<float2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
             SV_CUDA_TRY(cudaFuncSetAttribute(k_expect<double2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
@@ -569,7 +569,7 @@ extern "C" sv_status sv_expect_pauli(sv_handle h, double *out) {
             SV_CUDA_TRY(cudaFuncSetAttribute(k_expect13<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
             SV_CUDA_TRY(cudaFuncSetAttribute(k_expect13<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
             SV_CUDA_TRY(cudaFuncSetAttribute(k_expect13<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-            configured = true;
+            attrs_set(configured, h->device);
         }
     }
     // The passes' tile sets depend only on which qubits earlier passes

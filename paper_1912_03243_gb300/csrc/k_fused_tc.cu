@@ -462,11 +462,11 @@ cudaError_t tc_launch(sv_state *h, const TcArgs &args, const void *dA) {
         if (e != cudaSuccess) return e;
     }
     const size_t smem = kTcGroups * (2 * size_t(kBBytes) + 2 * size_t(kStageBytes));
-    static bool configured = false;
-    if (!configured) {
+    static std::atomic<uint64_t> configured{0};
+    if (attrs_needed(configured, h->device)) {
         const cudaError_t e = cudaFuncSetAttribute(k_fused_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
         if (e != cudaSuccess) return e;
-        configured = true;
+        attrs_set(configured, h->device);
     }
     int sms = 0;
     const cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);

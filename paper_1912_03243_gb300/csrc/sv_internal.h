@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -24,6 +25,16 @@ bool fault_injected(const char *what);  // SV_FAULT_INJECT host-side hooks
 cudaError_t ensure_err_word(::sv_state *h);
 // Map a launch result (and the "launch" fault hook) to a status.
 sv_status check_launch(cudaError_t e, const char *what);
+
+// Kernel attributes (cudaFuncSetAttribute) belong to a device: one flag bit
+// per device records that a kernel family's attributes were set there.
+// Setting them twice is harmless, so concurrent first calls need no lock.
+inline bool attrs_needed(const std::atomic<uint64_t> &done, int device) {
+    return device < 0 || device >= 64 || !((done.load(std::memory_order_acquire) >> device) & 1u);
+}
+inline void attrs_set(std::atomic<uint64_t> &done, int device) {
+    if (device >= 0 && device < 64) done.fetch_or(uint64_t(1) << device, std::memory_order_release);
+}
 // Synchronise a stream (and honour the "sync" fault hook).
 sv_status sync_stream(cudaStream_t st, const char *what);
 
