@@ -102,6 +102,29 @@ def test_grid_6x4_all_amplitudes(S, orc):
     assert 1 - f <= 1e-5
 
 
+@pytest.mark.parametrize("depth,cuts", [(6, 4), (12, 8), (18, 12)])
+def test_form_error_study(S, orc, record_property, depth, cuts):
+    """Error of each decomposition against the full FP64 state as the number
+    of cut gates grows (5x4 grid, rows 0-1 | 2-4, all 2^20 amplitudes): the
+    projector form (weight 1, bounded factors) and Eq. 2 (weight 1/2 per cut,
+    factors of size r^2 = 1 + sqrt 2 whose terms cancel).  Both stay inside the
+    tolerance; the measured errors are recorded."""
+    c = C.grid_circuit(5, 4, depth, 1)
+    mask = C.grid_partition_mask(5, 4, 2)
+    z = np.arange(1 << 20, dtype=np.uint64)
+    full = orc.run(c)
+    scale = np.max(np.abs(full))
+    for form in (0, 1):
+        got, s = S.sv_cut_amplitudes(c, 20, mask, z, form=form)
+        assert s == cuts
+        err = float(np.max(np.abs(got - full)) / scale)
+        f = abs(np.vdot(full, got)) ** 2 / (np.vdot(full, full).real * np.vdot(got, got).real)
+        record_property(f"form{form}_S{cuts}_max_rel_err", err)
+        record_property(f"form{form}_S{cuts}_infidelity", float(1 - f))
+        print(f"form-error S={cuts} form={form} max|d|/max|amp|={err:.3e} 1-F={1 - f:.3e}")
+        assert err <= 1e-5 and 1 - f <= 1e-5
+
+
 def test_grid_6x8_48q_both_forms(S):
     """The 48-qubit 6x8 grid, depth 8, S = 8: 256 branches x 2 halves of 2^24
     amplitudes (2 x 2^32 batched complex64), 1024 seeded output bit strings.
