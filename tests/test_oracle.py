@@ -84,6 +84,41 @@ def test_uniform_superposition(orc, n):
             assert abs(q - golden[a]) < 1e-13, (i, a, q)
 
 
+@pytest.mark.parametrize("n,seed", [(1, 3), (4, 5), (7, 11)])
+def test_expect_pauli_product_states(orc, n, seed):
+    """For a product state psi = phi_{n-1} (x) ... (x) phi_0 (qubit j = index
+    bit j) the expectation values of qubit j are its Bloch vector, from its
+    own two amplitudes (a, b): <sigma^x> = 2 Re(conj(a) b), <sigma^y> =
+    2 Im(conj(a) b), <sigma^z> = |a|^2 - |b|^2 (sigma^y = [[0, -i], [i, 0]]).
+    Random phases make every sign matter."""
+    rng = np.random.default_rng(seed)
+    phis = []
+    for _ in range(n):
+        v = rng.normal(size=2) + 1j * rng.normal(size=2)
+        phis.append(v / np.linalg.norm(v))
+    psi = np.array([1.0 + 0j])
+    for j in range(n):
+        psi = np.kron(phis[j], psi)  # qubit j becomes the more significant factor
+    for j, (a, b) in enumerate(phis):
+        want = {"x": 2 * (np.conj(a) * b).real, "y": 2 * (np.conj(a) * b).imag, "z": abs(a) ** 2 - abs(b) ** 2}
+        for alpha in "xyz":
+            assert abs(orc.expect_pauli(psi, j, alpha) - want[alpha]) < 1e-13, (j, alpha)
+
+
+def test_expect_pauli_basis_and_eigenstates(orc):
+    """Basis state |b>: <sigma^z_i> = 1 - 2 b_i, <sigma^x_i> = <sigma^y_i> = 0;
+    single-qubit eigenstates |+>, |->, |+i>, |-i> give +-1 on their axis."""
+    n, b = 6, 0b101100
+    psi = np.zeros(1 << n, dtype=np.complex128)
+    psi[b] = 1.0
+    for i in range(n):
+        assert orc.expect_pauli(psi, i, "z") == 1 - 2 * ((b >> i) & 1)
+        assert orc.expect_pauli(psi, i, "x") == 0 and orc.expect_pauli(psi, i, "y") == 0
+    r = 1 / math.sqrt(2)
+    for state, axis, val in (([r, r], "x", 1), ([r, -r], "x", -1), ([r, 1j * r], "y", 1), ([r, -1j * r], "y", -1)):
+        assert abs(orc.expect_pauli(np.array(state, dtype=np.complex128), 0, axis) - val) < 1e-15
+
+
 @pytest.mark.parametrize("n", [2, 3, 8, 16])
 def test_ghz(orc, n):
     """Sec. 3: H(0) + CNOT chain gives (|0..0> + |1..1>)/sqrt(2)."""
