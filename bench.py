@@ -305,6 +305,20 @@ def fp32_ops_per_amplitude(circ) -> int:
     return sum(FP32_OPS.get(name.upper(), 8) for name, _, _ in circ.gates)
 
 
+def binding_roofline(hbm, fp32, fp32_floor_s, hbm_floor_s, steps):
+    """The roofline object headed by the binding roof: the FP32 lanes when the
+    step's minimum FP32 time exceeds its minimum HBM time, else HBM; the other
+    roof is kept beside it, and both minimum times (ms per step) with it."""
+    if fp32_floor_s > hbm_floor_s:
+        out = dict(fp32, **{k: hbm[k] for k in ("kernel", "launches", "avg_launch_ms", "share_of_step", "traffic")})
+        out["hbm"] = {k: hbm[k] for k in ("bound", "achieved", "peak", "unit", "frac", "peak_kind",
+                                           "frac_of_nominal_8tbs", "bytes_per_launch")}
+    else:
+        out = dict(hbm, fp32=fp32)
+    out["floors_ms"] = {"fp32": 1e3 * fp32_floor_s / steps, "hbm": 1e3 * hbm_floor_s / steps}
+    return out
+
+
 def dominant_roofline(info, per_launch, steps, peak, peak_kind, n=None):
     tot, cnt, byt = {}, {}, {}
     for k in range(steps):
@@ -678,15 +692,7 @@ def run_ours(args, world, rank, local):
                                  "(two additions on half the amplitudes), 0 for CZ"}
         fp32_floor = ops / peak_ops
         hbm_floor = sum(byt.values()) / (hbm_peak * 1e9)
-        if fp32_floor > hbm_floor:
-            hbm_part = {k: roofline[k] for k in ("bound", "achieved", "peak", "unit", "frac", "peak_kind",
-                                                  "frac_of_nominal_8tbs", "bytes_per_launch")}
-            head = {k: roofline[k] for k in ("kernel", "launches", "avg_launch_ms", "share_of_step", "traffic")}
-            roofline = dict(roofline_fp32, **head)
-            roofline["floors_ms"] = {"fp32": 1e3 * fp32_floor / args.steps, "hbm": 1e3 * hbm_floor / args.steps}
-            roofline["hbm"] = hbm_part
-        else:
-            roofline["fp32"] = roofline_fp32
+        roofline = binding_roofline(roofline, roofline_fp32, fp32_floor, hbm_floor, args.steps)
 
     # accuracy: the circuit followed by its inverse returns |0...0>
     inv = state.plan(C.inverse_circuit(circ), mode)

@@ -1,0 +1,54 @@
+"""Host logic of bench.py (no GPU): which roof heads the roofline object, and
+the FP32 lane operations a circuit needs at least."""
+
+import os
+import sys
+
+import pytest
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+
+import bench  # noqa: E402
+from paper_1912_03243_gb300 import circuits as C  # noqa: E402
+
+HBM = {"bound": "hbm", "achieved": 3490.0, "peak": 6690.8, "unit": "GB/s", "frac": 3490.0 / 6690.8,
+       "traffic": 6.8e10, "kernel": "svp<f32,13,5>", "launches": 55, "avg_launch_ms": 19.7,
+       "bytes_per_launch": 6.87e10, "peak_kind": "measured", "frac_of_nominal_8tbs": 3490.0 / 8000.0,
+       "share_of_step": 1.0}
+FP32 = {"bound": "alu", "achieved": 26.4, "peak": 40.27, "unit": "T FP32 lane-ops/s", "frac": 26.4 / 40.27}
+
+
+def test_fp32_roof_heads_when_its_floor_is_longer():
+    r = bench.binding_roofline(HBM, FP32, fp32_floor_s=0.710, hbm_floor_s=0.565, steps=5)
+    assert r["bound"] == "alu" and r["frac"] == FP32["frac"] and r["unit"] == FP32["unit"]
+    # the launch facts and the DRAM traffic of the dominant kernel stay at the top
+    for k in ("kernel", "launches", "avg_launch_ms", "share_of_step", "traffic"):
+        assert r[k] == HBM[k]
+    assert r["hbm"]["bound"] == "hbm" and r["hbm"]["frac"] == HBM["frac"]
+    assert r["floors_ms"] == pytest.approx({"fp32": 142.0, "hbm": 113.0})
+    assert "fp32" not in r
+
+
+def test_hbm_roof_heads_otherwise():
+    r = bench.binding_roofline(HBM, FP32, fp32_floor_s=0.2, hbm_floor_s=0.565, steps=5)
+    assert r["bound"] == "hbm" and r["frac"] == HBM["frac"] and r["fp32"] == FP32
+    assert r["floors_ms"] == pytest.approx({"fp32": 40.0, "hbm": 113.0})
+
+
+def test_fp32_ops_per_amplitude():
+    """2 per H / SX / SY (one addition per real component), 1 per T (two
+    additions on half the amplitudes), 0 for sign flips and permutations, 8
+    for a dense 2x2."""
+    c = C.Circuit(4)
+    for name, qs in (("H", (0,)), ("T", (1,)), ("CZ", (0, 1)), ("SX", (2,)), ("SY", (3,)), ("X", (0,)),
+                     ("SWAP", (1, 2))):
+        c.add(name, *qs)
+    c.add("U", 0, params=(1, 0, 0, 0, 0, 0, 1, 0))
+    assert bench.fp32_ops_per_amplitude(c) == 2 + 1 + 0 + 2 + 2 + 0 + 0 + 8
+
+
+def test_benchmark_circuit_ops():
+    c = C.random_circuit(32, 24, 1)
+    names = [g[0] for g in c.gates]
+    assert bench.fp32_ops_per_amplitude(c) == 2 * sum(n in ("H", "SX", "SY") for n in names) + names.count("T")
+    assert bench.fp32_ops_per_amplitude(c) == 1331
