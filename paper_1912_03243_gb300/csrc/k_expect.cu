@@ -593,8 +593,14 @@ extern "C" sv_status sv_expect_pauli(sv_handle h, double *out) {
         }
     }
     const size_t per_pass = size_t(kExVals) * grid;
-    double *d_part = nullptr;
-    SV_CUDA_TRY(cudaMalloc(&d_part, sizeof(double) * per_pass * tiles.size()));
+    if (h->expect_cap < per_pass * tiles.size()) {  // handle scratch, grown on demand
+        if (h->d_expect) SV_CUDA_TRY(cudaFree(h->d_expect));
+        h->d_expect = nullptr;
+        h->expect_cap = 0;
+        SV_CUDA_TRY(cudaMalloc(&h->d_expect, sizeof(double) * per_pass * tiles.size()));
+        h->expect_cap = per_pass * tiles.size();
+    }
+    double *d_part = h->d_expect;
     sv_status s = SV_OK;
     for (size_t pass = 0; pass < tiles.size() && s == SV_OK; ++pass) {
         const std::vector<int> &tile = tiles[pass];
@@ -633,7 +639,6 @@ extern "C" sv_status sv_expect_pauli(sv_handle h, double *out) {
                                               cudaMemcpyDeviceToHost, h->stream);
         s = e != cudaSuccess ? cuda_status(e, "cudaMemcpyAsync") : sync_stream(h->stream, "sv_expect_pauli");
     }
-    cudaFree(d_part);
     if (s) return s;
     // x, y of a qubit from the first pass that has it in its tile, z from pass 0
     std::vector<double> x(size_t(n), 0.0), y(size_t(n), 0.0), z(size_t(n), 0.0);

@@ -238,6 +238,7 @@ sv_status sv_free(sv_handle h) {
     if (h->d_amps) cudaFree(h->d_amps);
     if (h->d_mat) cudaFree(h->d_mat);
     if (h->d_err) cudaFree(h->d_err);
+    if (h->d_expect) cudaFree(h->d_expect);
     delete h;
     return SV_OK;
 }

@@ -104,6 +104,8 @@ struct sv_state {
     size_t gather_cap = 0;
     void *d_mat = nullptr;         // fused-gate matrix upload (64 KB)
     int *d_err = nullptr;          // device error word (bounded waits that gave up)
+    double *d_expect = nullptr;    // expectation-value partial sums (per pass and CTA)
+    size_t expect_cap = 0;         // their capacity in doubles
     int live_plans = 0;
 };
 
