@@ -207,12 +207,14 @@ sv_status sv_norm(sv_handle h, double *out);
  * out: caller-owned host array of 3n doubles, out[3 i + alpha] with
  * alpha 0 = x, 1 = y, 2 = z; not divided by the norm.  Works on SV_C64,
  * SV_C128 and SV_ENC2B (decoded on the fly, codes untouched).  Read-only
- * passes over the state in tiles of 2^13 amplitudes (2^12 for SV_C128) that
- * keep the low qubits (4; the 8 in-block ones for SV_ENC2B): 1 +
- * ceil((n - 13) / 9) passes for SV_C64.  Per-tile sums in the storage
- * precision, FP64 across tiles.  Synchronises.  Errors: SV_ERR_ARG (NULL),
- * SV_ERR_UNSUPPORTED (more than 40 qubits outside one tile), SV_ERR_OOM or
- * SV_ERR_CUDA (a small partial-sum buffer is allocated per call). */
+ * passes over the state in tiles of 2^13 amplitudes (2^12 for SV_C128):
+ * the first holds qubits 0..12, each later one keeps the low qubits (3, or
+ * SV_EXPECT_LOW in 3..8; the 8 in-block ones for SV_ENC2B) and takes the
+ * next uncovered ones: 1 + ceil((n - 13) / 10) passes for SV_C64.  Sums in
+ * the storage precision over a few tiles, FP64 beyond.  Synchronises.
+ * Errors: SV_ERR_ARG (NULL), SV_ERR_UNSUPPORTED (more than 40 qubits outside
+ * one tile), SV_ERR_OOM (the partial-sum scratch, kept in the handle and
+ * grown on first use) or SV_ERR_CUDA. */
 sv_status sv_expect_pauli(sv_handle h, double *out);
 
 /* Raw copy of the whole state between device and host memory (bytes must be
