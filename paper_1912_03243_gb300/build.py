@@ -20,6 +20,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libsv.so")
+WORKER_SRC = os.path.join(HERE, "csrc", "worker", "nvrtc_worker.cpp")
+WORKER = os.path.join(HERE, "sv_nvrtc_worker")  # next to libsv.so, where the library looks for it
 INCLUDE = os.path.join(ROOT, "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -85,7 +87,29 @@ def build(verbose: bool = False, ptxas_v: bool = False) -> str:
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)
+    build_worker(cuda_lib)
     return LIB
+
+
+def build_worker(cuda_lib: str) -> str:
+    """The NVRTC compile worker (an executable: NVRTC serialises compilations
+    within a process, so the library runs several workers at once)."""
+    h = hashlib.sha1()
+    for p in (WORKER_SRC, os.path.join(CSRC, "nvrtc_opts.h")):
+        with open(p, "rb") as f:
+            h.update(f.read())
+    h.update(platform.machine().encode())
+    stamp = os.path.join(BUILD, f"sv_nvrtc_worker.{h.hexdigest()[:16]}")
+    if not (os.path.exists(stamp) and os.path.exists(WORKER)):
+        tmp = WORKER + f".tmp{os.getpid()}"
+        cmd = [nvcc(), "-O2", "-std=c++17", "-o", tmp, WORKER_SRC, "-lnvrtc", "-Xlinker", f"-rpath={cuda_lib}"]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"worker build failed:\n{r.stdout}\n{r.stderr}")
+        os.replace(tmp, WORKER)
+        with open(stamp, "w"):
+            pass
+    return WORKER
 
 
 if __name__ == "__main__":

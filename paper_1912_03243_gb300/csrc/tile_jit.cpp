@@ -20,8 +20,15 @@
 //         constant register offsets), apply the segment's ops, scatter;
 //   store: 16-byte chunks back to HBM.
 // Conditions on thread or CTA index bits become selects, not branches.
+#include <dlfcn.h>
+#include <fcntl.h>
 #include <nvrtc.h>
+#include <spawn.h>
+#include <sys/stat.h>
+#include <sys/wait.h>
+#include <unistd.h>
 
+#include <cerrno>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -37,8 +44,11 @@
 #include <unordered_map>
 #include <vector>
 
+#include "nvrtc_opts.h"
 #include "plan.h"
 #include "tile.h"
+
+extern char **environ;
 
 namespace sv {
 
@@ -546,23 +556,22 @@ struct JitEntry {
 std::mutex g_jit_mu;
 std::unordered_map<std::string, JitEntry> g_jit;  // key: device + source
 
+bool jit_verbose() {
+    const char *ve = std::getenv("SV_JIT_VERBOSE");
+    return ve && ve[0] == '1';
+}
+
+// In-process NVRTC compile of one pass (SV_JIT_VERBOSE=1 prints ptxas
+// resource usage, registers and spills, to stderr).
 std::string compile_cubin(const std::string &src, std::string *err) {
     nvrtcProgram prog;
     if (nvrtcCreateProgram(&prog, src.c_str(), "sv_pass.cu", 0, nullptr, nullptr) != NVRTC_SUCCESS) {
         *err = "nvrtcCreateProgram failed";
         return {};
     }
-    // SV_JIT_VERBOSE=1 prints ptxas resource usage (registers, spills) to stderr
-    const char *ve = std::getenv("SV_JIT_VERBOSE");
-    const bool verbose = ve && ve[0] == '1';
-    const char *opts[] = {"--gpu-architecture=sm_103a", "--std=c++17", "--ptxas-options=-v"};
-    const nvrtcResult r = nvrtcCompileProgram(prog, verbose ? 3 : 2, opts);
-    if (verbose && std::getenv("SV_JIT_DUMP")) {  // SV_JIT_DUMP=<file>: append the generated source
-        if (FILE *f = std::fopen(std::getenv("SV_JIT_DUMP"), "a")) {
-            std::fputs(src.c_str(), f);
-            std::fclose(f);
-        }
-    }
+    const bool verbose = jit_verbose();
+    const nvrtcResult r = nvrtcCompileProgram(prog, verbose ? kPassNvrtcOptsVerbose : kPassNvrtcOptsQuiet,
+                                              kPassNvrtcOpts);
     if (verbose) {
         size_t n = 0;
         nvrtcGetProgramLogSize(prog, &n);
@@ -587,6 +596,132 @@ std::string compile_cubin(const std::string &src, std::string *err) {
     return cubin;
 }
 
+// ---------------------------------------------------------------- compile workers
+// NVRTC serialises compilations inside one process (threads do not overlap),
+// so passes compile in separate worker processes, several at once: the
+// executable sv_nvrtc_worker next to this library (SV_JIT_WORKER overrides
+// the path; SV_JIT_PROCS=0 compiles in-process).  The worker runs the same
+// NVRTC with the same options, so the cubins are the same.  posix_spawn
+// starts it without copying this process (safe with the CUDA context and
+// other threads).  If no worker can be started, the compile runs in-process.
+
+void jit_anchor() {}
+
+std::string worker_path() {
+    const char *procs = std::getenv("SV_JIT_PROCS");
+    if (procs && procs[0] == '0') return std::string();
+    if (const char *w = std::getenv("SV_JIT_WORKER")) return std::string(w);
+    static const std::string beside_library = [] {
+        Dl_info info;
+        if (!dladdr(reinterpret_cast<void *>(&jit_anchor), &info) || !info.dli_fname) return std::string();
+        const std::string lib = info.dli_fname;
+        const size_t slash = lib.rfind('/');
+        const std::string dir = slash == std::string::npos ? std::string(".") : lib.substr(0, slash);
+        return dir + "/sv_nvrtc_worker";
+    }();
+    return beside_library;
+}
+
+std::string read_file(const std::string &path) {
+    std::string out;
+    if (FILE *f = std::fopen(path.c_str(), "rb")) {
+        char buf[65536];
+        size_t n;
+        while ((n = std::fread(buf, 1, sizeof buf, f)) > 0) out.append(buf, n);
+        std::fclose(f);
+    }
+    return out;
+}
+
+// Compile src in a worker.  Returns false if no worker could be started (the
+// caller compiles in-process); true otherwise, with *cubin set, or empty and
+// *err set when the compile itself failed.
+bool compile_in_worker(const std::string &src, std::string *cubin, std::string *err) {
+    const std::string worker = worker_path();
+    if (worker.empty() || access(worker.c_str(), X_OK) != 0) return false;
+    const char *tmp = std::getenv("TMPDIR");
+    std::string dir = std::string(tmp && tmp[0] ? tmp : "/tmp") + "/sv_jit_XXXXXX";
+    if (!mkdtemp(&dir[0])) return false;
+    const std::string src_path = dir + "/pass.cu", out_path = dir + "/pass.cubin", log_path = dir + "/log";
+    bool started = false;
+    if (FILE *f = std::fopen(src_path.c_str(), "wb")) {
+        const bool ok = std::fwrite(src.data(), 1, src.size(), f) == src.size();
+        if (std::fclose(f) == 0 && ok) {
+            const bool verbose = jit_verbose();
+            posix_spawn_file_actions_t fa;
+            posix_spawn_file_actions_init(&fa);
+            posix_spawn_file_actions_addopen(&fa, 0, "/dev/null", O_RDONLY, 0);
+            posix_spawn_file_actions_addopen(&fa, 1, "/dev/null", O_WRONLY, 0);
+            if (!verbose) posix_spawn_file_actions_addopen(&fa, 2, log_path.c_str(), O_WRONLY | O_CREAT | O_TRUNC, 0600);
+            std::string a0 = worker, a1 = src_path, a2 = out_path, a3 = verbose ? "1" : "0";
+            char *argv[] = {&a0[0], &a1[0], &a2[0], &a3[0], nullptr};
+            pid_t pid = 0;
+            if (posix_spawn(&pid, worker.c_str(), &fa, nullptr, argv, environ) == 0) {
+                int status = 0;
+                pid_t w;
+                do {
+                    w = waitpid(pid, &status, 0);
+                } while (w < 0 && errno == EINTR);
+                if (w == pid) {
+                    started = true;
+                    if (WIFEXITED(status) && WEXITSTATUS(status) == 0) {
+                        *cubin = read_file(out_path);
+                        if (cubin->empty()) *err = "the compile worker wrote no cubin";
+                    } else {
+                        *err = "compile worker failed: " + read_file(log_path).substr(0, 400);
+                    }
+                }
+            }
+            posix_spawn_file_actions_destroy(&fa);
+        }
+    }
+    std::remove(src_path.c_str());
+    std::remove(out_path.c_str());
+    std::remove(log_path.c_str());
+    rmdir(dir.c_str());
+    return started;
+}
+
+// Compile one pass: in a worker, else in-process.  SV_JIT_VERBOSE=1 with
+// SV_JIT_DUMP=<file> appends the generated source to that file.
+std::string compile_pass(const std::string &src, std::string *err) {
+    if (jit_verbose() && std::getenv("SV_JIT_DUMP")) {
+        static std::mutex dump_mu;
+        std::lock_guard<std::mutex> lock(dump_mu);
+        if (FILE *f = std::fopen(std::getenv("SV_JIT_DUMP"), "a")) {
+            std::fputs(src.c_str(), f);
+            std::fclose(f);
+        }
+    }
+    std::string cubin;
+    if (compile_in_worker(src, &cubin, err)) return cubin;
+    return compile_cubin(src, err);
+}
+
+// Compile src[j] for every j in todo, as many at once as there are hardware
+// threads; cubin[j] empty and err[j] set for a failure.
+void compile_many(const std::vector<std::string> &src, const std::vector<int> &todo, std::vector<std::string> *cubin,
+                  std::vector<std::string> *err) {
+    const unsigned hw = std::thread::hardware_concurrency();
+    const size_t nthreads = std::min<size_t>(todo.size(), hw ? hw : 4);
+    std::vector<std::thread> pool;
+    size_t next = 0;
+    std::mutex qmu;
+    for (size_t k = 0; k < nthreads; ++k)
+        pool.emplace_back([&]() {
+            for (;;) {
+                size_t j;
+                {
+                    std::lock_guard<std::mutex> l(qmu);
+                    if (next >= todo.size()) return;
+                    j = size_t(todo[next++]);
+                }
+                (*cubin)[j] = compile_pass(src[j], &(*err)[j]);
+            }
+        });
+    for (auto &th : pool) th.join();
+}
+
 template <typename R>
 sv_status jit_plan_impl(const TilePlan<R> &tp, std::vector<void *> *fns) {
     // make sure the runtime has made the primary context current
@@ -608,24 +743,7 @@ sv_status jit_plan_impl(const TilePlan<R> &tp, std::vector<void *> *fns) {
         }
     }
     // compile the misses in parallel (NVRTC programs are independent)
-    unsigned hw = std::thread::hardware_concurrency();
-    const size_t nthreads = std::min<size_t>(todo.size(), hw ? hw : 4);
-    std::vector<std::thread> pool;
-    size_t next = 0;
-    std::mutex qmu;
-    for (size_t k = 0; k < nthreads; ++k)
-        pool.emplace_back([&]() {
-            for (;;) {
-                size_t j;
-                {
-                    std::lock_guard<std::mutex> l(qmu);
-                    if (next >= todo.size()) return;
-                    j = size_t(todo[next++]);
-                }
-                cubin[j] = compile_cubin(src[j], &err[j]);
-            }
-        });
-    for (auto &th : pool) th.join();
+    compile_many(src, todo, &cubin, &err);
     for (int j : todo) {
         if (cubin[size_t(j)].empty()) {
             set_error("NVRTC compile of pass %d failed: %s", j, err[size_t(j)].c_str());
@@ -655,13 +773,19 @@ sv_status jit_plan_impl(const TilePlan<R> &tp, std::vector<void *> *fns) {
 
 template <typename R>
 sv_status compile_check_impl(const TilePlan<R> &tp) {
-    for (size_t i = 0; i < tp.passes.size(); ++i) {
-        std::string err;
-        if (compile_cubin(gen_pass(tp, i), &err).empty()) {
-            set_error("NVRTC compile of pass %zu failed: %s", i, err.c_str());
+    const size_t np = tp.passes.size();
+    std::vector<std::string> src(np), cubin(np), err(np);
+    std::vector<int> todo(np);
+    for (size_t i = 0; i < np; ++i) {
+        src[i] = gen_pass(tp, i);
+        todo[i] = int(i);
+    }
+    compile_many(src, todo, &cubin, &err);
+    for (size_t i = 0; i < np; ++i)
+        if (cubin[i].empty()) {
+            set_error("NVRTC compile of pass %zu failed: %s", i, err[i].c_str());
             return SV_ERR_CUDA;
         }
-    }
     return SV_OK;
 }
 

@@ -101,6 +101,18 @@ def test_tiled_plans_compile_for_sm103a(L):
         sv.sv_plan_stats(C.random_circuit(8, 2, 1), 8, "c64")
 
 
+@pytest.mark.parametrize("env", [{}, {"SV_JIT_PROCS": "0"}, {"SV_JIT_WORKER": "/nonexistent/sv_nvrtc_worker"}])
+def test_pass_compiles_in_workers_or_in_process(L, monkeypatch, env):
+    """Tiled passes compile in worker processes (NVRTC serialises work within
+    one process), in-process with SV_JIT_PROCS=0, and in-process when no
+    worker can be started."""
+    assert os.access(os.path.join(os.path.dirname(sv.__file__), "sv_nvrtc_worker"), os.X_OK)
+    for k, v in env.items():
+        monkeypatch.setenv(k, v)
+    g, p, s = sv.sv_plan_stats(C.random_circuit(14, 4, 9), 14, "c64", compile=True)
+    assert g == 14 * 4 + 2 * 7 + 2 * 6 and p >= 1
+
+
 @pytest.mark.parametrize("name,n,gates,passes,segments", [("random", 32, 1140, 11, 32), ("random", 28, 996, 9, 30),
                                                          ("random", 30, 712, 8, 23), ("qft", 32, 564, 6, 17)])
 def test_planner_does_not_regress(L, name, n, gates, passes, segments):
