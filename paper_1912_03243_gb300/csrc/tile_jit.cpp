@@ -25,9 +25,11 @@
 #include <nvrtc.h>
 #include <spawn.h>
 #include <sys/stat.h>
+#include <sys/utsname.h>
 #include <sys/wait.h>
 #include <unistd.h>
 
+#include <atomic>
 #include <cerrno>
 #include <cmath>
 #include <cstdio>
@@ -682,8 +684,82 @@ bool compile_in_worker(const std::string &src, std::string *cubin, std::string *
     return started;
 }
 
-// Compile one pass: in a worker, else in-process.  SV_JIT_VERBOSE=1 with
-// SV_JIT_DUMP=<file> appends the generated source to that file.
+// ---------------------------------------------------------------- disk cache
+// Compiled passes persist across processes: one file per pass source under
+// SV_JIT_CACHE (a directory; "0" turns the cache off), by default the folder
+// _jit_cache beside this library.  The file name hashes the host machine,
+// the NVRTC version, the options and the source; the file holds the source
+// and the cubin, and a load is taken only when the stored source equals the
+// current one byte for byte (a hash collision or a damaged file is a miss).
+// Files are written under a temporary name and renamed into place, so a
+// reader never sees a partial one.
+
+constexpr char kCacheMagic[] = "SVJIT1\n";
+
+std::string cache_dir() {
+    const char *e = std::getenv("SV_JIT_CACHE");
+    if (e && e[0] == '0' && e[1] == '\0') return std::string();
+    std::string dir;
+    if (e && e[0]) {
+        dir = e;
+    } else {
+        Dl_info info;
+        if (!dladdr(reinterpret_cast<void *>(&jit_anchor), &info) || !info.dli_fname) return std::string();
+        const std::string lib = info.dli_fname;
+        const size_t slash = lib.rfind('/');
+        dir = (slash == std::string::npos ? std::string(".") : lib.substr(0, slash)) + "/_jit_cache";
+    }
+    // create the directory and its missing parents (0700)
+    for (size_t k = 1; k <= dir.size(); ++k)
+        if (k == dir.size() || dir[k] == '/') mkdir(dir.substr(0, k).c_str(), 0700);
+    struct stat st;
+    if (stat(dir.c_str(), &st) != 0 || !S_ISDIR(st.st_mode) || access(dir.c_str(), W_OK | X_OK) != 0)
+        return std::string();
+    return dir;
+}
+
+std::string cache_file(const std::string &dir, const std::string &src) {
+    int major = 0, minor = 0;
+    nvrtcVersion(&major, &minor);
+    struct utsname un;
+    std::string tag = std::string(uname(&un) == 0 ? un.machine : "?") + " nvrtc " + std::to_string(major) + "." +
+                      std::to_string(minor);
+    for (int i = 0; i < kPassNvrtcOptsQuiet; ++i) tag += std::string(" ") + kPassNvrtcOpts[i];
+    uint64_t h = 1469598103934665603ull;  // FNV-1a, 64 bits
+    const std::string *parts[] = {&tag, &src};
+    for (const std::string *part : parts)
+        for (unsigned char ch : *part) h = (h ^ ch) * 1099511628211ull;
+    char name[40];
+    std::snprintf(name, sizeof name, "/%016llx.bin", static_cast<unsigned long long>(h));
+    return dir + name;
+}
+
+bool cache_load(const std::string &path, const std::string &src, std::string *cubin) {
+    const std::string data = read_file(path);
+    const std::string head = std::string(kCacheMagic) + std::to_string(src.size()) + "\n";
+    if (data.size() <= head.size() + src.size() || data.compare(0, head.size(), head) != 0 ||
+        data.compare(head.size(), src.size(), src) != 0)
+        return false;
+    *cubin = data.substr(head.size() + src.size());
+    return true;
+}
+
+void cache_store(const std::string &path, const std::string &src, const std::string &cubin) {
+    static std::atomic<uint64_t> seq{0};
+    const std::string tmp = path + ".tmp" + std::to_string(getpid()) + "." + std::to_string(seq.fetch_add(1));
+    FILE *f = std::fopen(tmp.c_str(), "wb");
+    if (!f) return;
+    const std::string head = std::string(kCacheMagic) + std::to_string(src.size()) + "\n";
+    bool ok = std::fwrite(head.data(), 1, head.size(), f) == head.size();
+    ok = ok && std::fwrite(src.data(), 1, src.size(), f) == src.size();
+    ok = ok && std::fwrite(cubin.data(), 1, cubin.size(), f) == cubin.size();
+    ok = (std::fclose(f) == 0) && ok;
+    if (!ok || std::rename(tmp.c_str(), path.c_str()) != 0) std::remove(tmp.c_str());
+}
+
+// Compile one pass: from the disk cache, else in a worker, else in-process.
+// SV_JIT_VERBOSE=1 with SV_JIT_DUMP=<file> appends the generated source to
+// that file.
 std::string compile_pass(const std::string &src, std::string *err) {
     if (jit_verbose() && std::getenv("SV_JIT_DUMP")) {
         static std::mutex dump_mu;
@@ -693,9 +769,13 @@ std::string compile_pass(const std::string &src, std::string *err) {
             std::fclose(f);
         }
     }
+    const std::string dir = cache_dir();
+    const std::string path = dir.empty() ? std::string() : cache_file(dir, src);
     std::string cubin;
-    if (compile_in_worker(src, &cubin, err)) return cubin;
-    return compile_cubin(src, err);
+    if (!path.empty() && !jit_verbose() && cache_load(path, src, &cubin)) return cubin;
+    if (!compile_in_worker(src, &cubin, err)) cubin = compile_cubin(src, err);
+    if (!path.empty() && !cubin.empty()) cache_store(path, src, cubin);
+    return cubin;
 }
 
 // Compile src[j] for every j in todo, as many at once as there are hardware

@@ -113,6 +113,26 @@ def test_pass_compiles_in_workers_or_in_process(L, monkeypatch, env):
     assert g == 14 * 4 + 2 * 7 + 2 * 6 and p >= 1
 
 
+def test_compiled_pass_disk_cache(L, monkeypatch, tmp_path):
+    """Compiled passes are kept on disk, one file per pass source (the source
+    and the cubin); a damaged file is a miss and is written again; with
+    SV_JIT_CACHE=0 nothing is written."""
+    c = C.random_circuit(16, 6, 12)
+    monkeypatch.setenv("SV_JIT_CACHE", str(tmp_path))
+    g, p, s = sv.sv_plan_stats(c, 16, "c64", compile=True)
+    files = sorted(tmp_path.iterdir())
+    assert len(files) == p and all(f.read_bytes().startswith(b"SVJIT1\n") for f in files)
+    good = files[0].read_bytes()
+    files[0].write_bytes(good[: len(good) // 2])
+    assert sv.sv_plan_stats(c, 16, "c64", compile=True) == (g, p, s)
+    assert files[0].read_bytes() == good  # recompiled: the same source gives the same cubin
+    off = tmp_path / "off"
+    off.mkdir()
+    monkeypatch.setenv("SV_JIT_CACHE", "0")
+    sv.sv_plan_stats(C.random_circuit(15, 5, 13), 15, "c64", compile=True)
+    assert not any(off.iterdir()) and sorted(tmp_path.iterdir()) == sorted(files + [off])
+
+
 @pytest.mark.parametrize("name,n,gates,passes,segments", [("random", 32, 1140, 11, 32), ("random", 28, 996, 9, 30),
                                                          ("random", 30, 712, 8, 23), ("qft", 32, 564, 6, 17)])
 def test_planner_does_not_regress(L, name, n, gates, passes, segments):
