@@ -34,10 +34,12 @@
  *   sv_last_error() returns a thread-local message for the last failure.
  * Sizes.  1 <= n <= 40 for SV_C64/SV_C128 and 1 <= n <= 40 for SV_ENC2B,
  *   further limited by free device memory (checked before allocating).
- * Fault injection (host side, for tests): the environment variable
- *   SV_FAULT_INJECT=alloc|launch|sync makes the next allocation, launch or
- *   synchronisation report SV_ERR_OOM / SV_ERR_CUDA without touching the
- *   GPU.
+ * Fault injection (host side, for tests): while the environment variable
+ *   SV_FAULT_INJECT=alloc|launch|sync is set, every allocation, launch or
+ *   synchronisation reports SV_ERR_OOM / SV_ERR_CUDA without touching the
+ *   GPU; SV_FAULT_INJECT=tc_wait makes the tensor-core kernel skip its MMA
+ *   so that its bounded wait runs out (SV_ERR_TIMEOUT at the next
+ *   synchronising call, the context stays usable).
  */
 #ifndef SV_H
 #define SV_H
