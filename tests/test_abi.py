@@ -113,6 +113,28 @@ def test_pass_compiles_in_workers_or_in_process(L, monkeypatch, env):
     assert g == 14 * 4 + 2 * 7 + 2 * 6 and p >= 1
 
 
+def test_plain_c_client(L, tmp_path):
+    """The boundary is a C ABI: a C99 program (tests/c_abi_probe.c) compiles
+    against include/sv.h with warnings as errors, links libsv.so and runs its
+    host-only calls, with the same answers as the Python binding."""
+    import subprocess
+
+    here = os.path.dirname(os.path.abspath(__file__))
+    libdir = os.path.dirname(os.path.abspath(sv.__file__))
+    exe = str(tmp_path / "c_abi_probe")
+    cmd = ["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-I", os.path.join(os.path.dirname(here), "include"),
+           os.path.join(here, "c_abi_probe.c"), "-L", libdir, "-lsv", f"-Wl,-rpath,{libdir}", "-lm", "-o", exe]
+    subprocess.run(cmd, check=True, capture_output=True, text=True)
+    out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout.split("\n")
+    rows = {line.split()[0]: line.split()[1:] for line in out if line}
+    assert int(rows["bytes_c64_20"][0]) == sv.sv_bytes_required(20, "c64") == 8 << 20
+    assert int(rows["bytes_enc_20"][0]) == sv.sv_bytes_required(20, "enc2b")
+    assert rows["gate_H"][0] == "1"
+    assert float(rows["gate_H"][1]) == pytest.approx(2 ** -0.5) and float(rows["gate_H"][2]) == pytest.approx(-(2 ** -0.5))
+    assert rows["plan"][0] == "0" and rows["plan"][1] == "4" and int(rows["plan"][2]) >= 1
+    assert rows["bad"][0] != "0" and rows["bad"][1] == "message"
+
+
 def test_compiled_pass_disk_cache(L, monkeypatch, tmp_path):
     """Compiled passes are kept on disk, one file per pass source (the source
     and the cubin); a damaged file is a miss and is written again; with
