@@ -481,3 +481,38 @@ def test_cut_multi_ghz_128(orc):
         assert s == 7
         assert np.allclose(amps[:2], 1 / math.sqrt(2), atol=1e-14)
         assert np.max(np.abs(amps[2:])) < 1e-14
+
+
+# ------------------------------------------------------- input generators
+
+def test_grid_circuit_structure():
+    """The grid workload (reading R8): on a 6x8 grid at depth 8 the CZ
+    patterns A B C D E F A B give 124 CZs; rows 0-2 | 3-5 are crossed only by
+    the vertical edges (2, c)-(3, c) of C and D, S = 8, and each half keeps
+    58 CZs; the 6x4 check grid has S = 4 at depth 8 and S = 8 at depth 12.
+    Every layer's CZs act on disjoint qubits between grid neighbours, and the
+    six patterns together hold every neighbour edge exactly once."""
+
+    def counts(rows, cols, depth):
+        c = C.grid_circuit(rows, cols, depth, 1)
+        mask = C.grid_partition_mask(rows, cols, 3)
+        cz = [qs for name, qs, _ in c.gates if name == "CZ"]
+        cut = [e for e in cz if ((mask >> e[0]) & 1) != ((mask >> e[1]) & 1)]
+        in_a = [e for e in cz if (mask >> e[0]) & 1 and (mask >> e[1]) & 1]
+        return len(cz), len(cut), len(in_a), len(cz) - len(cut) - len(in_a)
+
+    assert counts(6, 8, 8) == (124, 8, 58, 58)
+    assert counts(6, 4, 8)[1] == 4 and counts(6, 4, 12)[1] == 8
+    for rows, cols in ((6, 8), (5, 4), (3, 3)):
+        seen = []
+        for pat in "ABCDEF":
+            edges = C.grid_edges(rows, cols, pat)
+            qubits = [q for e in edges for q in e]
+            assert len(qubits) == len(set(qubits)), pat  # one CZ per qubit per layer
+            for a, b in edges:
+                (ra, ca), (rb, cb) = divmod(a, cols), divmod(b, cols)
+                assert abs(ra - rb) + abs(ca - cb) == 1  # grid neighbours
+            seen += [tuple(sorted(e)) for e in edges]
+        every = {(r * cols + c, r * cols + c + 1) for r in range(rows) for c in range(cols - 1)}
+        every |= {(r * cols + c, (r + 1) * cols + c) for r in range(rows - 1) for c in range(cols)}
+        assert sorted(seen) == sorted(every)
