@@ -516,3 +516,26 @@ def test_grid_circuit_structure():
         every = {(r * cols + c, r * cols + c + 1) for r in range(rows) for c in range(cols - 1)}
         every |= {(r * cols + c, (r + 1) * cols + c) for r in range(rows - 1) for c in range(cols)}
         assert sorted(seen) == sorted(every)
+
+
+def test_random_circuit_structure():
+    """The random family (reading R3): each layer is one gate from
+    {H, T, SX, SY} on every qubit in ascending order, then CZ on (2i, 2i+1)
+    in even layers and (2i+1, 2i+2) in odd layers; a seed fixes the circuit,
+    and the draws use all four gates."""
+    n, depth = 9, 6
+    c = C.random_circuit(n, depth, 4)
+    assert c.gates == C.random_circuit(n, depth, 4).gates
+    assert c.gates != C.random_circuit(n, depth, 5).gates
+    i, names = 0, set()
+    for layer in range(depth):
+        for q in range(n):
+            name, qs, _ = c.gates[i]
+            assert qs == (q,) and name in ("H", "T", "SX", "SY")
+            names.add(name)
+            i += 1
+        start = 0 if layer % 2 == 0 else 1
+        for a in range(start, n - 1, 2):
+            assert c.gates[i][0] == "CZ" and c.gates[i][1] == (a, a + 1)
+            i += 1
+    assert i == len(c.gates) and names == {"H", "T", "SX", "SY"}
