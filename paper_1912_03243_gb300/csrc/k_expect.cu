@@ -8,8 +8,9 @@
 // 2^m amplitudes (the low qubits plus chosen ones, as in the tiled gate
 // passes) and sums these over every tile qubit; <sigma^z> of the qubits
 // outside the tile follows from each tile's total probability, signed by the
-// tile number's bits.  Persistent CTAs accumulate per tile in FP32 (FP64 for
-// complex128) and across tiles in FP64; the host adds the CTAs' partials.
+// tile number's bits.  Persistent CTAs accumulate in FP32 (FP64 for
+// complex128) per tile, or per chunk of 8 tiles in the 13-bit kernel, and in
+// FP64 beyond; the host adds the CTAs' partials.
 #include <algorithm>
 #include <cstdlib>
 #include <vector>
