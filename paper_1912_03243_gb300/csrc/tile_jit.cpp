@@ -635,14 +635,18 @@ std::string read_file(const std::string &path) {
     return out;
 }
 
+std::string cache_dir();
+
 // Compile src in a worker.  Returns false if no worker could be started (the
 // caller compiles in-process); true otherwise, with *cubin set, or empty and
 // *err set when the compile itself failed.
 bool compile_in_worker(const std::string &src, std::string *cubin, std::string *err) {
     const std::string worker = worker_path();
     if (worker.empty() || access(worker.c_str(), X_OK) != 0) return false;
+    // scratch files beside the disk cache when there is one, else in TMPDIR or /tmp
+    const std::string cache = cache_dir();
     const char *tmp = std::getenv("TMPDIR");
-    std::string dir = std::string(tmp && tmp[0] ? tmp : "/tmp") + "/sv_jit_XXXXXX";
+    std::string dir = (!cache.empty() ? cache : std::string(tmp && tmp[0] ? tmp : "/tmp")) + "/sv_jit_XXXXXX";
     if (!mkdtemp(&dir[0])) return false;
     const std::string src_path = dir + "/pass.cu", out_path = dir + "/pass.cubin", log_path = dir + "/log";
     bool started = false;

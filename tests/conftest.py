@@ -11,6 +11,9 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
     config.addinivalue_line("markers", "slow: takes more than a few seconds on CPU")
+    # temporary files of the tests stay inside the repository (git-ignored _build/)
+    if not config.option.basetemp:
+        config.option.basetemp = os.path.join(ROOT, "_build", "pytest_tmp")
 
 
 @pytest.fixture(scope="session")

@@ -151,6 +151,7 @@ def test_compiled_pass_disk_cache(L, monkeypatch, tmp_path):
     off = tmp_path / "off"
     off.mkdir()
     monkeypatch.setenv("SV_JIT_CACHE", "0")
+    monkeypatch.setenv("TMPDIR", str(off))  # the workers' scratch without a cache: created and removed
     sv.sv_plan_stats(C.random_circuit(15, 5, 13), 15, "c64", compile=True)
     assert not any(off.iterdir()) and sorted(tmp_path.iterdir()) == sorted(files + [off])
 
