@@ -52,3 +52,15 @@ def test_benchmark_circuit_ops():
     names = [g[0] for g in c.gates]
     assert bench.fp32_ops_per_amplitude(c) == 2 * sum(n in ("H", "SX", "SY") for n in names) + names.count("T")
     assert bench.fp32_ops_per_amplitude(c) == 1331
+
+
+@pytest.mark.parametrize("kernel", ["svp", "k_gate_across", "k_fused_tc", "k_enc_gate_across"])
+def test_profiles_match_the_sources(kernel):
+    """Every kernel the bench reports a roofline for has a committed ncu summary
+    whose source hash matches the current source (a stale one reads as no
+    traffic); its DRAM bytes per amplitude are near the algorithmic 16 (4 for
+    the two-byte code)."""
+    traffic, path = bench.traffic_from_profiles(kernel, 28)
+    assert traffic is not None and path is not None
+    per_amp = traffic / 2 ** 28
+    assert (3.0 < per_amp < 4.5) if kernel == "k_enc_gate_across" else (14.0 < per_amp < 17.0)
