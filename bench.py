@@ -225,12 +225,162 @@ def run_reference(args, world, rank):
 
 
 # ----------------------------------------------------------------- ncu traffic
+#
+# A committed ncu summary stays valid while the code it measured is unchanged.
+# For a kernel of a .cu file that code is the kernel's own text: its
+# definition plus every namespace-level definition it uses (device helpers,
+# constants, structs, also from the local headers the file includes), with
+# comments and whitespace dropped, so that host-only edits and comments do not
+# invalidate a capture.  For the compiled tile passes it is the generated
+# source of the passes of the profiled case.
+
+def _strip_comments(src: str) -> str:
+    out, i, n = [], 0, len(src)
+    while i < n:
+        c = src[i]
+        if c == '"':
+            j = i + 1
+            while j < n and src[j] != '"':
+                j += 2 if src[j] == "\\" else 1
+            out.append(src[i:j + 1])
+            i = j + 1
+        elif src.startswith("//", i):
+            j = src.find("\n", i)
+            i = n if j < 0 else j
+        elif src.startswith("/*", i):
+            j = src.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+        else:
+            out.append(c)
+            i += 1
+    return "".join(out)
+
+
+def _top_level_chunks(src: str) -> list:
+    """Namespace-level constructs of comment-free C++ source: function
+    definitions, structs and declarations ending in ';' (preprocessor lines
+    dropped, namespace and extern "C" braces transparent)."""
+    import re
+
+    src = "\n".join(ln for ln in src.split("\n") if not ln.lstrip().startswith("#"))
+    chunks, stack, start, i, n = [], [], 0, 0, len(src)
+    while i < n:
+        c = src[i]
+        if c == '"':
+            j = i + 1
+            while j < n and src[j] != '"':
+                j += 2 if src[j] == "\\" else 1
+            i = j + 1
+            continue
+        if c == "{":
+            if "blk" not in stack and re.search(r'(namespace\s*\w*|extern\s*"C")\s*$', src[start:i]):
+                stack.append("ns")
+                start = i + 1
+            else:
+                stack.append("blk")
+        elif c == "}":
+            kind = stack.pop() if stack else "ns"
+            if kind == "ns":
+                start = i + 1
+            elif "blk" not in stack:
+                j = i + 1
+                m = re.match(r"\s*;", src[j:])
+                if m:
+                    j += m.end()
+                chunks.append(src[start:j])
+                start = i = j
+                continue
+        elif c == ";" and "blk" not in stack:
+            chunks.append(src[start:i + 1])
+            start = i + 1
+        i += 1
+    return [c.strip() for c in chunks if c.strip()]
+
+
+_NOT_NAMES = {"__launch_bounds__", "__align__", "alignas", "decltype", "sizeof", "static_assert", "if", "for",
+              "while", "switch", "return", "template", "asm", "defined"}
+
+
+def _chunk_names(ch: str) -> set:
+    import re
+
+    head = ch.split("{", 1)[0]
+    head = re.sub(r"template\s*<[^{]*?>\s*", "", head, count=1)
+    m = re.match(r"\s*(?:struct|class|union|enum)\s+(?:class\s+)?(\w+)", head)
+    if m:
+        return {m.group(1)}
+    for m in re.finditer(r"(\w+)\s*\(", head):
+        if m.group(1) not in _NOT_NAMES:
+            if "=" in head[:m.start()]:
+                break
+            return {m.group(1)}
+    m = re.search(r"(\w+)\s*(?:\[[^\]]*\]\s*)*(?:=|;|\{)", head + ";")
+    return {m.group(1)} if m else set()
+
+
+def kernel_text(path: str, kernel: str, read=None) -> str:
+    """The text of __global__ function `kernel` of the .cu file at path and
+    of every namespace-level definition it uses, transitively (from the file
+    and the local headers it includes), comments and whitespace normalised."""
+    import re
+
+    def _read(p):
+        try:
+            with open(p) as f:
+                return f.read()
+        except OSError:
+            return None
+
+    read = read or _read
+    texts, seen = [], set()
+
+    def add(p):
+        if p in seen:
+            return
+        seen.add(p)
+        s = read(p)
+        if s is None:
+            return
+        texts.append(s)
+        for inc in re.findall(r'#include\s+"([^"]+)"', s):
+            add(os.path.normpath(os.path.join(os.path.dirname(p), inc)))
+
+    add(path)
+    named = [(_chunk_names(c), c) for s in texts for c in _top_level_chunks(_strip_comments(s))]
+    want, done, out = {kernel}, set(), []
+    while want:
+        name = want.pop()
+        done.add(name)
+        for names, c in named:
+            if name in names and c not in out:
+                out.append(c)
+                want |= set(re.findall(r"[A-Za-z_]\w*", c)) - done
+    order = {c: k for k, (_, c) in enumerate(named)}
+    out.sort(key=order.get)
+    return "\n".join(" ".join(c.split()) for c in out)
+
+
+def kernel_text_sha1(kv: dict):
+    """Current hash of the code a summary measured (None if it cannot be
+    computed here)."""
+    if kv.get("kernel_case"):
+        try:
+            from paper_1912_03243_gb300 import sv
+
+            return hashlib.sha1(sv.tiled_pass_sources(kv["kernel_case"]).encode()).hexdigest()
+        except Exception:
+            return None
+    src = os.path.join(ROOT, "paper_1912_03243_gb300", "csrc", kv.get("source", ""))
+    if not os.path.exists(src):
+        return None
+    return hashlib.sha1(kernel_text(src, kv.get("function", kv["kernel"])).encode()).hexdigest()
+
 
 def traffic_from_profiles(kernel: str, n: int):
     """DRAM bytes per launch from a committed ncu summary: a summary file under
     profiles/ carries lines 'kernel: <name>', 'dram_bytes_per_amplitude: <x>'
-    and 'source_sha1: <sha1 of the kernel's .cu at capture>'; stale summaries
-    (source changed since) give None."""
+    and 'kernel_text_sha1: <hash of the measured code at capture>'; a summary
+    whose code has changed since gives None."""
     for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
         kv = {}
         with open(path) as f:
@@ -240,12 +390,16 @@ def traffic_from_profiles(kernel: str, n: int):
                     kv[k.strip().strip("-* `")] = v.strip().strip("`")
         if kv.get("kernel") != kernel or "dram_bytes_per_amplitude" not in kv:
             continue
-        src = os.path.join(ROOT, "paper_1912_03243_gb300", "csrc", kv.get("source", ""))
-        if not os.path.exists(src):
-            continue
-        with open(src, "rb") as f:
-            if hashlib.sha1(f.read()).hexdigest() != kv.get("source_sha1"):
+        if "kernel_text_sha1" in kv:
+            if kernel_text_sha1(kv) != kv["kernel_text_sha1"]:
                 return None, path
+        else:
+            src = os.path.join(ROOT, "paper_1912_03243_gb300", "csrc", kv.get("source", ""))
+            if not os.path.exists(src):
+                continue
+            with open(src, "rb") as f:
+                if hashlib.sha1(f.read()).hexdigest() != kv.get("source_sha1"):
+                    return None, path
         return float(kv["dram_bytes_per_amplitude"]) * (1 << n), path
     return None, None
 

@@ -133,7 +133,9 @@ sv_status sv_apply_gate(sv_handle h, int target, int control, const double *U);
  * A_hi B_lo + A_lo B_hi) and FP32 accumulation; smaller SV_C64 states in
  * FP32 and SV_C128 in FP64 on the CUDA cores.  The tensor-core kernel's only
  * wait is bounded; if it gives up, the next synchronising call returns
- * SV_ERR_TIMEOUT.  Errors: SV_ERR_ARG, SV_ERR_DTYPE (SV_ENC2B). */
+ * SV_ERR_TIMEOUT, after which the state and the CUDA context are undefined
+ * (MMAs still in flight may write freed tensor memory) and must be
+ * discarded.  Errors: SV_ERR_ARG, SV_ERR_DTYPE (SV_ENC2B). */
 sv_status sv_apply_fused(sv_handle h, int k, const int *qubits, const double *U);
 
 /* ---- circuits -------------------------------------------------------------- */
@@ -238,7 +240,13 @@ sv_status sv_copy_from_host(sv_handle h, const void *src, size_t bytes);
  * address (cudaGetSymbolAddress) with the device current, so make the first
  * call before any stream capture.  Every call shares the array: calls that
  * overlap on the GPU (other threads, other streams) race.  Synchronises the
- * stream.  Errors: SV_ERR_ARG, SV_ERR_CUDA. */
+ * stream.  The state pointer is checked on the host before any copy or
+ * launch: it must be device memory of the current device
+ * (cudaPointerGetAttributes), aligned to 16 bytes for SV_C128 and 8 bytes
+ * otherwise, and, where the driver reports the allocation's extent, hold
+ * sv_bytes_required(n, dt) bytes from the pointer on; a host pointer, a
+ * pointer of another device, a misaligned or too-short buffer is SV_ERR_ARG
+ * with a message.  Errors: SV_ERR_ARG, SV_ERR_CUDA. */
 sv_status sv_amplitudes_noalloc(const void *state, int n, sv_dtype dt, size_t m, const uint64_t *idx,
                                 double *out, void *stream);
 

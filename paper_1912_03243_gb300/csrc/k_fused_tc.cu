@@ -27,6 +27,13 @@
 //   %globaltimer) -> each warp reads its 32 TMEM lanes with tcgen05.ld and
 //   scatters FP32 results back to the staging tile -> coalesced 16-byte
 //   stores to HBM.
+// Timeout: the wait for the MMAs is bounded by %globaltimer.  When it runs
+// out, the group stops, the CTA frees its tensor memory and the host sees
+// SV_ERR_TIMEOUT.  The test hook (skip_mma) issues no MMA, so nothing is in
+// flight then.  After a real timeout the committed MMAs may still be writing
+// the freed tensor memory and may later arrive on an mbarrier in shared
+// memory the CTA has released: the state and the CUDA context must then be
+// treated as undefined and discarded, not reused.
 // B operand layout (K-major, no swizzle): element (row, kk) at byte
 // (row%8)*16 + (kk%8)*2 + (kk/8)*128 + (row/8)*2048; leading-dimension byte
 // offset 128 (next 8 K-elements), stride-dimension byte offset 2048 (next 8

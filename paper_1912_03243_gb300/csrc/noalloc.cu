@@ -12,6 +12,8 @@
 // The array is sized for kNoAllocMaxAmps indices (24 B each: 1.5 MiB) and,
 // like every file-scope __device__ variable, occupies memory on every GPU
 // that loads the library until the process exits.  All calls share it.
+#include <cuda.h>  // driver types for cuMemGetAddressRange (fetched at run time, not linked)
+
 #include <mutex>
 
 #include "sv_internal.h"
@@ -46,6 +48,65 @@ sv_status scratch_for_current_device(unsigned char **out) {
         g_scratch_ptr[dev] = static_cast<unsigned char *>(p);
     }
     *out = g_scratch_ptr[dev];
+    return SV_OK;
+}
+
+// cuMemGetAddressRange, looked up once through the runtime (the library links
+// only the static runtime); nullptr if the driver does not offer it.
+typedef CUresult (*AddrRangeFn)(CUdeviceptr *, size_t *, CUdeviceptr);
+AddrRangeFn addr_range_fn() {
+    static const AddrRangeFn fn = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuMemGetAddressRange", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            p = nullptr;
+        return reinterpret_cast<AddrRangeFn>(p);
+    }();
+    return fn;
+}
+
+// Host-side checks of the caller's state pointer, before anything touches
+// it: aligned for the widest access the gather makes, device memory of the
+// current device, and (where the driver reports the allocation's extent)
+// large enough for the whole n-qubit layout.  None of these calls allocates.
+sv_status check_state_pointer(const void *state, int n, sv_dtype dt) {
+    const size_t align = dt == SV_C128 ? 16 : 8;
+    if (reinterpret_cast<uintptr_t>(state) % align) {
+        set_error("state pointer %p is not %zu-byte aligned", state, align);
+        return SV_ERR_ARG;
+    }
+    int dev = -1;
+    SV_CUDA_TRY(cudaGetDevice(&dev));
+    cudaPointerAttributes attr{};
+    const cudaError_t e = cudaPointerGetAttributes(&attr, state);
+    if (e != cudaSuccess) {
+        cudaGetLastError();  // an invalid pointer is the caller's error, not a sticky one
+        set_error("state pointer %p is not device memory (%s)", state, cudaGetErrorString(e));
+        return SV_ERR_ARG;
+    }
+    if (attr.type != cudaMemoryTypeDevice) {
+        set_error("state pointer %p is not device memory (memory type %d)", state, int(attr.type));
+        return SV_ERR_ARG;
+    }
+    if (attr.device != dev) {
+        set_error("state pointer %p belongs to device %d, the current device is %d", state, attr.device, dev);
+        return SV_ERR_ARG;
+    }
+    if (AddrRangeFn fn = addr_range_fn()) {
+        CUdeviceptr base = 0;
+        size_t size = 0;
+        if (fn(&base, &size, CUdeviceptr(reinterpret_cast<uintptr_t>(state))) == CUDA_SUCCESS) {
+            const size_t need = sv_bytes_required(n, dt);
+            const size_t avail = size_t(base + size - CUdeviceptr(reinterpret_cast<uintptr_t>(state)));
+            if (need > avail) {
+                set_error("an n=%d state of dtype %d needs %zu bytes, the allocation holds %zu from %p", n, int(dt),
+                          need, avail, state);
+                return SV_ERR_ARG;
+            }
+        }
+    }
     return SV_OK;
 }
 
@@ -100,8 +161,10 @@ extern "C" sv_status sv_amplitudes_noalloc(const void *state, int n, sv_dtype dt
             set_error("index %llu at position %zu >= 2^%d", (unsigned long long)idx[j], j, n);
             return SV_ERR_ARG;
         }
+    sv_status s = check_state_pointer(state, n, dt);
+    if (s) return s;
     unsigned char *scratch = nullptr;
-    sv_status s = scratch_for_current_device(&scratch);
+    s = scratch_for_current_device(&scratch);
     if (s) return s;
     uint64_t *d_idx = reinterpret_cast<uint64_t *>(scratch);
     double2 *d_out = reinterpret_cast<double2 *>(scratch + kNoAllocMaxAmps * sizeof(uint64_t));

@@ -64,3 +64,37 @@ def test_profiles_match_the_sources(kernel):
     assert traffic is not None and path is not None
     per_amp = traffic / 2 ** 28
     assert (3.0 < per_amp < 4.5) if kernel == "k_enc_gate_across" else (14.0 < per_amp < 17.0)
+
+
+def test_kernel_text_ignores_comments_and_host_code(tmp_path):
+    """The validity hash of a profile covers the kernel and what it uses, not
+    comments, host functions or other kernels of the same file."""
+    hdr = tmp_path / "k.h"
+    hdr.write_text("#pragma once\nstruct Args { int n; };\nconstexpr int kUnused = 3;\n")
+    base = '''#include "k.h"
+namespace sv {
+namespace {
+constexpr int kW = 4;  // width
+__device__ __forceinline__ int twice(int x) { return 2 * x; }
+__global__ void __launch_bounds__(128) k_a(int *p, Args a) { p[threadIdx.x] = twice(a.n) + kW; }
+__global__ void k_b(int *p) { p[0] = 1; }
+}  // namespace
+int host_fn(int x) { return x + 1; }
+}  // namespace sv
+'''
+    src = tmp_path / "k.cu"
+
+    def h(text, header=None):
+        src.write_text(text)
+        if header is not None:
+            hdr.write_text(header)
+        return bench.kernel_text(str(src), "k_a")
+
+    ref = h(base)
+    assert "twice" in ref and "kW = 4" in ref and "struct Args" in ref and "k_b" not in ref and "host_fn" not in ref
+    assert h(base.replace("// width", "// a new comment\n/* block */")) == ref
+    assert h(base.replace("return x + 1;", "return x + 2;")) == ref          # host code
+    assert h(base.replace("p[0] = 1;", "p[0] = 2;")) == ref                  # another kernel
+    assert h(base.replace("2 * x", "3 * x")) != ref                          # a helper it calls
+    assert h(base.replace("kW = 4", "kW = 5")) != ref                        # a constant it uses
+    assert h(base, "#pragma once\nstruct Args { long n; };\nconstexpr int kUnused = 3;\n") != ref  # header struct
