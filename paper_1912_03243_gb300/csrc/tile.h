@@ -142,6 +142,9 @@ const char *tile_kernel_name(const sv_state *h);
 // The code-generation switches (environment) that shape a compiled pass, as
 // part of a plan-cache key.
 std::string tile_codegen_key();
+// Direct HBM I/O of complex64 passes (SV_TILE_DIRECT, default on): the first
+// segment loads from and the last stores to HBM straight from registers.
+bool direct_io_enabled();
 // Planner lookahead width (SV_PLAN_LOOKAHEAD, default 4; 0 = greedy).
 int plan_lookahead_width();
 // Segment (register set) lookahead width (SV_SEG_LOOKAHEAD, default 4; 0 =

@@ -108,12 +108,42 @@ bool packed_adds_enabled() {
     return !(e && e[0] == '0');
 }
 
+
 // CTAs per SM the pass kernels are compiled for (register budget); the
 // shared tile (64 KiB) allows up to 3.  SV_TILE_CTAS overrides.
 int tile_ctas_per_sm() {
     const char *e = std::getenv("SV_TILE_CTAS");
     const int v = e ? std::atoi(e) : 2;
     return v >= 1 && v <= 3 ? v : 2;
+}
+
+// Which ends of a pass go straight between HBM and registers: direct I/O on,
+// complex64, and lanes of the first (last) segment that cover at least the 3
+// lowest tile bits (8 lanes x 8 B: whole 32-byte sectors per warp access);
+// otherwise that end is staged through shared memory with 16-byte copies.
+struct HbmIo {
+    bool load, store;
+    int nseg;
+};
+
+template <typename R>
+HbmIo hbm_io(const TilePlan<R> &tp, size_t pass) {
+    const TilePassArgs &pa = tp.passes[pass];
+    int first = -1, last = -1, nseg = 0;
+    for (int i = pa.op_begin; i < pa.op_end; ++i)
+        if (tp.ops[size_t(i)].type == TOP_SEG) {
+            if (first < 0) first = tp.ops[size_t(i)].a;
+            last = tp.ops[size_t(i)].a;
+            ++nseg;
+        }
+    const bool on = sizeof(R) == 4 && direct_io_enabled() && first >= 0;
+    auto contiguous = [&](int sidx) {
+        const TileSeg &sg = tp.segs[size_t(sidx)];
+        uint32_t lanes = 0;
+        for (int k = 0; k < 5 && k < tp.m - tp.rb; ++k) lanes |= 1u << sg.tpos[k];
+        return (lanes & 7u) == 7u && pa.lc >= 3;
+    };
+    return HbmIo{on && contiguous(first), on && contiguous(last), nseg};
 }
 
 template <typename R>
@@ -169,20 +199,40 @@ std::string gen_pass(const TilePlan<R> &tp, size_t pass) {
     // its bits, and the global offsets are recomputed for the store
     // (short live ranges leave the registers to the amplitudes)
     o << "  const u32 t = threadIdx.x;\n  const u64 cta = blockIdx.x;\n";
-    o << "  {\n  u64 g0 = 0;\n";
-    emit_deposit(o, "g0", "cta", opos, pa.nouter, "u64");
-    emit_deposit(o, "g0", "t", tpos, tbits, "u64");
-    o << "  const u32 s0 = swz(t);\n";
-    for (int i = 0; i < iters; ++i)
-        o << "  cpa16(smem + ((s0 ^ " << si[size_t(i)] << "u) << 4), psi + (g0 | " << gi[size_t(i)] << "ull));\n";
-    o << "  }\n";
-    o << "  asm volatile(\"cp.async.commit_group;\\ncp.async.wait_group 0;\\n\" ::: \"memory\");\n";
-    o << "  __syncthreads();\n";
+    const HbmIo io = hbm_io(tp, pass);
+    if (!io.load) {
+        o << "  {\n  u64 g0 = 0;\n";
+        emit_deposit(o, "g0", "cta", opos, pa.nouter, "u64");
+        emit_deposit(o, "g0", "t", tpos, tbits, "u64");
+        o << "  const u32 s0 = swz(t);\n";
+        for (int i = 0; i < iters; ++i)
+            o << "  cpa16(smem + ((s0 ^ " << si[size_t(i)] << "u) << 4), psi + (g0 | " << gi[size_t(i)] << "ull));\n";
+        o << "  }\n";
+        o << "  asm volatile(\"cp.async.commit_group;\\ncp.async.wait_group 0;\\n\" ::: \"memory\");\n";
+        o << "  __syncthreads();\n";
+    }
+    // Global offset of a segment's registers: the CTA's outer bits and the
+    // thread's tile bits (at their global positions) in one per-thread base,
+    // plus a constant per register slot (disjoint bits, so + is |).
+    auto emit_thread_base = [&](const TileSeg &sg, const char *name) {
+        int gpos[kTileMaxQ];
+        for (int k = 0; k < tbits; ++k) gpos[k] = pa.tile_pos[sg.tpos[k]];
+        o << "  u64 " << name << " = 0;\n";
+        emit_deposit(o, name, "cta", opos, pa.nouter, "u64");
+        emit_deposit(o, name, "t", gpos, tbits, "u64");
+    };
+    auto reg_goff = [&](const TileSeg &sg, int v) {
+        unsigned long long g = 0;
+        for (int sl = 0; sl < G.RB; ++sl)
+            if (v >> sl & 1) g |= 1ull << pa.tile_pos[sg.rpos[sl]];
+        return g;
+    };
     const char *SYNC = "  __syncthreads();\n";
     o << "  " << RT << " xr[" << G.NR << "], xi[" << G.NR << "];\n  u32 jt = 0, pj = 0;\n";
     (void)0;
 
     int cur_seg = -1;
+    bool first_seg = true;
     uint32_t pv[kTileMaxRegs] = {0};
     // The stored value of register v is the amplitude divided by
     //   sgn[v] * prod(rsg[v]) * 2^(-me[v] / 2):
@@ -312,14 +362,25 @@ std::string gen_pass(const TilePlan<R> &tp, size_t pass) {
             emit_deposit(o, "jt", "t", pos, tbits, "u32");
             if (sizeof(R) == 4) o << "  pj = (swz(jt >> 1) << 1) | (jt & 1u);\n";
             else o << "  pj = swz(jt);\n";
+            const bool from_hbm = io.load && first_seg;
+            first_seg = false;
+            if (from_hbm) {
+                o << "  {\n";
+                emit_thread_base(sg, "gq");
+            }
             for (int v = 0; v < G.NR; ++v) {
                 uint32_t d = 0;
                 for (int s = 0; s < G.RB; ++s)
                     if (v >> s & 1) d |= 1u << sg.rpos[s];
                 pv[v] = Geo<R>::phys(d);
-                o << "  { " << C2T << " a = sm[pj ^ " << pv[v] << "u]; xr[" << v << "] = a.x; xi[" << v
-                  << "] = a.y; }\n";
+                if (from_hbm)
+                    o << "  { const " << C2T << " a = psi[gq + " << reg_goff(sg, v) << "ull]; xr[" << v
+                      << "] = a.x; xi[" << v << "] = a.y; }\n";
+                else
+                    o << "  { " << C2T << " a = sm[pj ^ " << pv[v] << "u]; xr[" << v << "] = a.x; xi[" << v
+                      << "] = a.y; }\n";
             }
+            if (from_hbm) o << "  }\n";
             continue;
         }
         // runtime condition on thread / CTA bits (branch-free select)
@@ -533,6 +594,24 @@ std::string gen_pass(const TilePlan<R> &tp, size_t pass) {
               << sel(nbr, "br") << "; " << bi << " = " << sel(nbi, "bi") << "; }\n";
         }
     }
+    if (io.store) {
+        // the last segment's registers go straight back to HBM
+        if (cur_seg >= 0) {
+            const TileSeg &sg = tp.segs[size_t(cur_seg)];
+            o << "  {\n";
+            emit_thread_base(sg, "gq");
+            for (int v = 0; v < G.NR; ++v) {
+                if (!rsg[v].empty() || !rph[v].empty() || me[v] != 0) materialise(v);
+                const char *neg = sgn[v] < 0 ? "-" : "";
+                o << "  psi[gq + " << reg_goff(sg, v) << "ull] = make_" << C2T << "(" << neg << "xr[" << v << "], "
+                  << neg << "xi[" << v << "]);\n";
+                sgn[v] = 1;
+            }
+            o << "  }\n";
+        }
+        o << "}\n";
+        return o.str();
+    }
     if (cur_seg >= 0) {
         scatter();
         o << SYNC;
@@ -557,6 +636,15 @@ struct JitEntry {
 
 std::mutex g_jit_mu;
 std::unordered_map<std::string, JitEntry> g_jit;  // key: device + source
+std::unordered_map<const void *, int> g_jit_smem;   // dynamic shared memory of each compiled pass
+
+// Shared memory a generated pass uses: the whole tile, unless direct HBM I/O
+// leaves it nothing to do (at most one segment).
+template <typename R>
+int pass_smem_bytes(const TilePlan<R> &tp, size_t pass) {
+    const HbmIo io = hbm_io(tp, pass);
+    return io.load && io.store && io.nseg <= 1 ? 0 : (1 << tp.m) * int(2 * sizeof(R));
+}
 
 bool jit_verbose() {
     const char *ve = std::getenv("SV_JIT_VERBOSE");
@@ -842,13 +930,14 @@ sv_status jit_plan_impl(const TilePlan<R> &tp, std::vector<void *> *fns) {
             cudaError_t ce = cudaLibraryLoadData(&e.lib, cubin[size_t(j)].data(), nullptr, nullptr, 0, nullptr,
                                                  nullptr, 0);
             if (ce == cudaSuccess) ce = cudaLibraryGetKernel(&e.fn, e.lib, "svp");
-            const int smem = (1 << tp.m) * int(2 * sizeof(R));
+            const int smem = pass_smem_bytes(tp, size_t(j));
             // a cudaKernel_t is accepted wherever a kernel symbol is
-            if (ce == cudaSuccess)
+            if (ce == cudaSuccess && smem > 0)
                 ce = cudaFuncSetAttribute(reinterpret_cast<const void *>(e.fn),
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
             if (ce != cudaSuccess) return cuda_status(ce, "loading a compiled pass");
             it = g_jit.emplace(key[size_t(j)], e).first;
+            g_jit_smem[reinterpret_cast<const void *>(e.fn)] = smem;
         }
         (*fns)[size_t(j)] = reinterpret_cast<void *>(it->second.fn);
     }
@@ -875,8 +964,20 @@ sv_status compile_check_impl(const TilePlan<R> &tp) {
 
 }  // namespace
 
+// Direct HBM I/O: the first segment loads its register amplitudes straight
+// from global memory and the last one stores them straight back, so shared
+// memory carries only the transpositions between segments (a one-segment
+// pass uses none).  SV_TILE_DIRECT=0 stages the whole tile through shared
+// memory with cp.async on the way in and out instead.  complex64 only (the
+// complex128 passes keep the staged form).
+bool direct_io_enabled() {
+    const char *e = std::getenv("SV_TILE_DIRECT");
+    return !(e && e[0] == '0');
+}
+
 std::string tile_codegen_key() {
-    return "f32x2=" + std::to_string(int(packed_adds_enabled())) + ",ctas=" + std::to_string(tile_ctas_per_sm());
+    return "f32x2=" + std::to_string(int(packed_adds_enabled())) + ",ctas=" + std::to_string(tile_ctas_per_sm()) +
+           ",direct=" + std::to_string(int(direct_io_enabled()));
 }
 
 sv_status jit_tile_plan(const TilePlan<float> &tp, std::vector<void *> *fns) { return jit_plan_impl(tp, fns); }
@@ -891,7 +992,12 @@ const char *tile_kernel_name(const sv_state *h) {
 
 cudaError_t launch_jit_pass(sv_state *h, void *fn, int n, int rb) {
     const int M = h->dt == SV_C64 ? kTileM64 : kTileM128;
-    const size_t tile_bytes = (size_t(1) << M) * (h->dt == SV_C64 ? 8u : 16u);
+    size_t tile_bytes = (size_t(1) << M) * (h->dt == SV_C64 ? 8u : 16u);
+    {
+        std::lock_guard<std::mutex> lock(g_jit_mu);
+        auto it = g_jit_smem.find(fn);
+        if (it != g_jit_smem.end()) tile_bytes = size_t(it->second);
+    }
     void *psi = h->data;
     void *args[] = {&psi};
     return cudaLaunchKernel(static_cast<const void *>(fn), dim3(1u << (n - M)), dim3(1u << (M - rb)), args, tile_bytes,

@@ -547,10 +547,10 @@ sv_status plan_tiles_one(const std::vector<PGate> &G, int n, const TileConfig &c
         while (!remaining.empty()) {
             const int sw = seg_lookahead_width();
             uint64_t Rset = sw > 0 ? rset_lookahead(G, remaining, T, rb, all, sw) : rset_first_fit(G, remaining, rb);
-            for (int k = 0; k < m && popc(Rset) < rb; ++k) {
-                // fill with tile bits above 0 first (keeps tile bit 0 free for lanes)
-                const int p = (k + 1) % m;
-                Rset |= uint64_t(1) << pa.tile_pos[p];
+            for (int k = m - 1; k >= 0 && popc(Rset) < rb; --k) {
+                // fill with the highest tile bits (keeps the low, contiguous
+                // ones free for lanes: coalesced HBM access)
+                Rset |= uint64_t(1) << pa.tile_pos[k];
             }
             std::vector<int> applicable, rest2;
             bF = bD = 0;
@@ -668,6 +668,29 @@ sv_status plan_tiles_one(const std::vector<PGate> &G, int n, const TileConfig &c
         }
         flush_scale();
         pa.op_end = int(out->ops.size());
+        if (cfg.c64 && direct_io_enabled()) {
+            // the first and last segments load from and store to HBM straight
+            // from registers when tile bits 0-2 are free for lanes: their lanes
+            // then take the lowest free tile bits (contiguous amplitudes), so a
+            // warp access covers whole sectors; otherwise that end is staged
+            // through shared memory and keeps the bank-friendly lane order
+            int first = -1, last = -1;
+            for (int i = pa.op_begin; i < pa.op_end; ++i)
+                if (out->ops[size_t(i)].type == TOP_SEG) {
+                    if (first < 0) first = out->ops[size_t(i)].a;
+                    last = out->ops[size_t(i)].a;
+                }
+            for (int sidx : {first, last}) {
+                if (sidx < 0) continue;
+                TileSeg &sg = out->segs[size_t(sidx)];
+                uint32_t reg = 0;
+                for (int sl = 0; sl < rb; ++sl) reg |= 1u << sg.rpos[sl];
+                if ((reg & 7u) != 0 || L < 3) continue;
+                int k = 0;
+                for (int b = 0; b < m; ++b)
+                    if (!(reg >> b & 1)) sg.tpos[k++] = uint8_t(b);
+            }
+        }
         out->passes.push_back(pa);
     }
     return SV_OK;
