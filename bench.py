@@ -51,7 +51,61 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the two-byte-code (35 qubits) and decomposition (48 qubits) measurements")
+    ap.add_argument("--profile-case", default=None, choices=sorted(PROFILE_CASES),
+                    help="run one small fixed invocation of a kernel family for a profiler capture, then exit")
     return ap.parse_args()
+
+
+# Small fixed invocations of each kernel family for profiler captures (the
+# commands in profiles/*.md): a few GB of device memory at most, states larger
+# than L2 (129 MB).
+PROFILE_CASES = {
+    "tiled": "28 qubits, random circuit depth 4, tiled passes (compiled kernels)",
+    "tiled24": "28 qubits, random circuit depth 24 (passes as full as at 32 qubits)",
+    "pergate": "28 qubits, random circuit depth 1, one launch per gate",
+    "enc": "28 qubits, two-byte code, random circuit depth 1",
+    "fused": "26 qubits, three dense 6-qubit blocks on the tensor cores (low, high and mixed qubits)",
+    "cut": "6x4 grid (24 qubits), depth 12, 8 cut CZs: 256 branches x 2 batched halves of 2^12 amplitudes each",
+    "expect": "28 qubits, uniform superposition, <sigma^alpha_i> of every qubit (complex64, then the two-byte code)",
+}
+
+
+def run_profile_case(case: str) -> None:
+    import numpy as np
+
+    from paper_1912_03243_gb300 import build
+    from paper_1912_03243_gb300 import circuits as C
+    from paper_1912_03243_gb300 import sv
+
+    build.build()
+    if case in ("tiled", "tiled24", "pergate"):
+        s = sv.StateVector(28, "c64")
+        depth = {"tiled": 4, "tiled24": 24, "pergate": 1}[case]
+        s.run(C.random_circuit(28, depth, 1), "pergate" if case == "pergate" else "tiled")
+    elif case == "enc":
+        s = sv.StateVector(28, "enc2b")
+        s.run(C.random_circuit(28, 1, 1), "pergate")
+    elif case == "fused":
+        s = sv.StateVector(26, "c64")
+        rng = np.random.default_rng(0)
+        z = rng.normal(size=(64, 64)) + 1j * rng.normal(size=(64, 64))
+        u, _ = np.linalg.qr(z)
+        for qs in ([0, 1, 2, 3, 4, 5], [20, 21, 22, 23, 24, 25], [3, 9, 14, 17, 21, 24]):
+            s.apply_fused(qs, u)
+    elif case == "expect":
+        s = sv.StateVector(28, "c64")
+        s.run(C.uniform_circuit(28), "tiled")
+        s.expect_pauli()
+        e = sv.StateVector(28, "enc2b")
+        e.encode_from(s)
+        e.expect_pauli()
+    else:  # cut
+        c = C.grid_circuit(6, 4, 12, 1)
+        sv.sv_cut_amplitudes(c, 24, C.grid_partition_mask(6, 4, 3), C.random_bitstrings(1024, 24, 7))
+        print("ok")
+        return
+    s.sync()
+    print("ok")
 
 
 def peaks():
@@ -737,42 +791,120 @@ def bench_ghz_sweep(S, C):
     return out
 
 
-def bench_cut42_depth(S, C):
+def cut_gates_42q(depth: int) -> int:
+    """Cut gates of the 6x7 grid (rows 0-2 | 3-5) after `depth` layers: the
+    vertical edges between rows 2 and 3 appear in patterns C (4 of them, even
+    columns) and D (3, odd columns), layers 2 and 3 of every six, so S grows
+    by 7 per six layers: 14 at depth 14, 18 at 15, 21 at 16-20, 25 at 21, 28
+    at 22-25."""
+    full, rem = divmod(depth, 6)
+    return 7 * full + (4 if rem > 2 else 0) + (3 if rem > 3 else 0)
+
+
+def bench_cut42_depth(S, C, budget_s: float = 240.0):
     """Decomposition at the paper's scale (Sec. 4, Fig. 4 workload shape): a
-    42-qubit 6x7 grid circuit cut between rows 0-2 and 3-5 (21 + 21 qubits)
-    at depths 4..14 (S = 7..14 cut gates), 1024 seeded amplitudes.  Branches
-    are summed in 2^p parts (p chosen so a half holds at most 2^31
-    amplitudes), one after another on this GPU.  Check: the projector and
-    Eq. 2 decompositions agree; the mean |amp|^2 times 2^42 is near 1."""
+    42-qubit 6x7 grid circuit cut between rows 0-2 and 3-5 (21 + 21 qubits),
+    1024 seeded amplitudes.  The branches are split into 2^p parts (p chosen
+    so a partition's batched vector holds at most 2^31 amplitudes) that run
+    one after another on this GPU with the same compiled passes and are summed
+    in FP64 on the device (one sv_cut_amplitudes_parts call); a first call on
+    one part compiles.  Depths 4-14 also run the Eq. 2 form (the two forms
+    must agree); 15 and 16 (S = 18, 21) the projector form, while the
+    projected time stays inside the budget.  Depths 17-20 have the same S as
+    16; 21-25 need 2^4 to 2^7 times the work of depth 16 (S = 25, 28) and are
+    out of reach of a bench run."""
     import numpy as np
     import torch
 
     n, mask = 42, C.grid_partition_mask(6, 7, 3)
     z = C.random_bitstrings(1024, n, 7)
-    rows = {}
-    for depth in (4, 6, 8, 10, 12, 14):
+    rows, spent = {}, 0.0
+    for depth in (4, 6, 8, 10, 12, 14, 15, 16):
         c = C.grid_circuit(6, 7, depth, 1)
-        _, s = S.sv_cut_amplitudes(c, n, mask, z[:0])  # m = 0: counts the cut gates only
+        _, s = S.sv_cut_amplitudes_part(c, n, mask, z[:0], 0, 16)  # m = 0: counts the cut gates only
+        assert s == cut_gates_42q(depth)
         plog = max(0, 21 + s - 31)
-        res, first = {}, {}
-        for form in (0, 1):
-            for rep in range(2):  # the first run also compiles the passes
-                torch.cuda.synchronize()
-                t0 = time.perf_counter()
-                acc = np.zeros(z.size, dtype=np.complex128)
-                for part in range(1 << plog):
-                    a, _ = S.sv_cut_amplitudes_part(c, n, mask, z, part, plog, form=form)
-                    acc += a
-                torch.cuda.synchronize()
-                (first if rep == 0 else res)[form] = (acc, time.perf_counter() - t0)
-        a0, t = res[0]
-        a1, t1 = res[1]
-        rows[depth] = {"gates": len(c), "cut_gates": s, "parts": 1 << plog, "s_per_call": t,
-                       "ms_per_gate": 1e3 * t / len(c), "s_per_call_eq2": t1, "s_first_call_with_compile": first[0][1],
-                       "forms_max_rel_diff": float(np.max(np.abs(a0 - a1)) / np.max(np.abs(a0))),
-                       "mean_abs2_times_2^42": float(np.mean(np.abs(a0) ** 2) * 2.0 ** n)}
-    return {"workload": "6x7 grid (42 qubits), rows 0-2 | 3-5, 1024 amplitudes, branch parts summed in turn",
-            "by_depth": rows}
+        parts = list(range(1 << plog))
+        res = {}
+        for form in ((0, 1) if depth <= 14 else (0,)):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            S.sv_cut_amplitudes_parts(c, n, mask, z, plog, [0], form=form)  # compiles, runs one part
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            est = (t1 - t0) * len(parts)
+            if depth > 14 and spent + est > budget_s:
+                rows[depth] = {"gates": len(c), "cut_gates": s, "parts": len(parts),
+                               "skipped": f"projected {est:.0f} s (one part with its compile x {len(parts)}) "
+                                          f"exceeds the remaining budget"}
+                break
+            a, _ = S.sv_cut_amplitudes_parts(c, n, mask, z, plog, parts, form=form)
+            torch.cuda.synchronize()
+            t = time.perf_counter() - t1
+            spent += time.perf_counter() - t0
+            res[form] = (a, t, t1 - t0)
+        if 0 not in res:
+            continue
+        a0, t, tc = res[0]
+        row = {"gates": len(c), "cut_gates": s, "parts": len(parts), "s_per_call": t,
+               "ms_per_gate": 1e3 * t / len(c), "s_first_part_with_compile": tc,
+               "mean_abs2_times_2^42": float(np.mean(np.abs(a0) ** 2) * 2.0 ** n)}
+        if 1 in res:
+            a1, t1_, _ = res[1]
+            row["s_per_call_eq2"] = t1_
+            row["forms_max_rel_diff"] = float(np.max(np.abs(a0 - a1)) / np.max(np.abs(a0)))
+        rows[depth] = row
+    return {"workload": "6x7 grid (42 qubits), rows 0-2 | 3-5, 1024 amplitudes, branch parts summed on the device",
+            "budget_s": budget_s, "by_depth": rows}
+
+
+def bench_batch(S, C):
+    """Many independent circuits of uneven size (64 random circuits, n drawn
+    from 13..22, depth 10, complex64) run as one batch (each member its own
+    chain of compiled passes in one CUDA graph) against the same members run
+    one after another on one stream (each plan replaying its own graph):
+    aggregate gates/s.  The states total 2^13..2^22 amplitudes each."""
+    import numpy as np
+    import torch
+
+    rng = np.random.default_rng(64)
+    ns = [int(x) for x in rng.integers(13, 23, size=64)]
+    circs = [C.random_circuit(n, 10, 500 + i) for i, n in enumerate(ns)]
+    states = [S.StateVector(n, "c64") for n in ns]
+    batch = S.Batch(states, circs)
+    plans = [st.plan(c, "tiled") for st, c in zip(states, circs)]
+    reps = 20
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            fn()
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) / reps
+
+    def one_by_one():
+        for p in plans:
+            p.execute()
+
+    t_batch = timed(batch.execute)
+    t_seq = timed(one_by_one)
+    gates = batch.gates
+    out = {"workload": f"64 random circuits, n in 13..22 (sum 2^n = {sum(1 << n for n in ns)} amplitudes), depth 10, "
+                       f"complex64, {gates} gates, {batch.launches} pass launches",
+           "batched": {"ms": 1e3 * t_batch, "gates_per_s": gates / t_batch, "gbs": batch.bytes / t_batch / 1e9},
+           "one_by_one": {"ms": 1e3 * t_seq, "gates_per_s": gates / t_seq, "gbs": batch.bytes / t_seq / 1e9},
+           "speedup": t_seq / t_batch, "uses_graph": batch.info().uses_graph,
+           "note": "host wall time per execution of all members (asynchronous launches, synchronised every 20)"}
+    for p in plans:
+        p.free()
+    batch.free()
+    for st in states:
+        st.free()
+    torch.cuda.empty_cache()
+    return out
 
 
 def bench_ghz128(S, C):
@@ -805,16 +937,6 @@ def bench_ghz128(S, C):
             "note": "end to end: host bit strings (2 GiB) in, 2^27 complex128 out"}
 
 
-def best_mode(S, state, circ):
-    for mode in ("tiled", "fused", "pergate"):
-        try:
-            p = state.plan(circ, mode)
-            return mode, p
-        except S.SVError:
-            continue
-    raise RuntimeError("no execution mode available")
-
-
 def run_ours(args, world, rank, local):
     import numpy as np
     import torch
@@ -828,8 +950,13 @@ def run_ours(args, world, rank, local):
     S.lib()
     circ, desc = workload(args)
     state = S.StateVector(args.n, "c64")
+    tuning = None
     if args.mode == "auto":
-        mode, plan = best_mode(S, state, circ)
+        # the library's autotuner times every candidate (tiled configurations,
+        # fused k = 3..6) on a scratch state and keeps the fastest
+        plan = state.plan(circ, "auto")
+        tuning = plan.tuning()
+        mode = tuning["chosen"].split()[0]
     else:
         mode, plan = args.mode, state.plan(circ, args.mode)
     info = plan.launch_info()
@@ -870,16 +997,31 @@ def run_ours(args, world, rank, local):
         ops = fp32_ops_per_amplitude(circ) * (1 << args.n) * args.steps
         secs = sum(tot.values()) / 1e3
         mhz = clocks.get("sm_mhz") or 2070.0
-        peak_ops = 152 * 128 * mhz * 1e6
+        sms = torch.cuda.get_device_properties(local).multi_processor_count
+        peak_ops = sms * 128 * mhz * 1e6
         roofline_fp32 = {"bound": "alu", "achieved": ops / secs / 1e12, "peak": peak_ops / 1e12,
                          "unit": "T FP32 lane-ops/s", "frac": ops / secs / peak_ops,
                          "ops_per_amplitude": fp32_ops_per_amplitude(circ),
-                         "peak_kind": "derived: 152 SMs x 128 FP32 lanes x the sampled SM clock",
+                         "peak_kind": f"derived: {sms} SMs (cudaDevAttrMultiProcessorCount) x 128 FP32 lanes x "
+                                      f"the sampled SM clock ({mhz:.0f} MHz)",
                          "note": "2 per amplitude for each H/SX/SY (one addition per real component), 1 for T "
                                  "(two additions on half the amplitudes), 0 for CZ"}
         fp32_floor = ops / peak_ops
         hbm_floor = sum(byt.values()) / (hbm_peak * 1e9)
         roofline = binding_roofline(roofline, roofline_fp32, fp32_floor, hbm_floor, args.steps)
+        # per pass: measured time against its own two floors (the pass's FP32
+        # work at the lane peak, its read + write of the state at the copy rate)
+        stats = plan.launch_stats()
+        per_pass = []
+        for i, (nm, b) in enumerate(info):
+            ms = sum(per_launch[k][i] for k in range(args.steps)) / args.steps
+            f32 = 1e3 * stats[i][0] * (1 << args.n) / peak_ops
+            hb = 1e3 * b / (hbm_peak * 1e9)
+            per_pass.append({"ms": round(ms, 3), "fp32_floor_ms": round(f32, 3), "hbm_floor_ms": round(hb, 3),
+                             "lane_ops_per_amp": stats[i][0], "segments": stats[i][1],
+                             "frac_of_binding_floor": round(max(f32, hb) / ms, 3)})
+        roofline["per_pass"] = per_pass
+        roofline["floors_ms"]["per_pass_max_sum"] = sum(max(r["fp32_floor_ms"], r["hbm_floor_ms"]) for r in per_pass)
 
     # accuracy: the circuit followed by its inverse returns |0...0>
     inv = state.plan(C.inverse_circuit(circ), mode)
@@ -929,7 +1071,7 @@ def run_ours(args, world, rank, local):
         t0 = time.perf_counter()
         for _ in range(args.steps):
             state.set_basis(0)
-            state.run(text, mode)
+            state.run(text, args.mode)
             amps = state.amplitudes(idx)
         torch.cuda.synchronize()
         te = max_over_ranks(world, time.perf_counter() - t0)
@@ -951,7 +1093,8 @@ def run_ours(args, world, rank, local):
         extras = {"enc2b_35q": bench_enc2b(S, C, args, world, hbm_peak, peak_kind), "cut_48q": bench_cut(S, C),
                   "qft_32q": bench_qft(S, C, hbm_peak), "h_sweep_32q": bench_h_sweep(S, C, hbm_peak, peak_kind),
                   "random_30q": bench_30q(S, C, hbm_peak), "expect_32q": bench_expect(S, C, hbm_peak),
-                  "ghz_sweep": bench_ghz_sweep(S, C), "cut_42q_depth": bench_cut42_depth(S, C),
+                  "ghz_sweep": bench_ghz_sweep(S, C), "batch_64": bench_batch(S, C),
+                  "cut_42q_depth": bench_cut42_depth(S, C),
                   "ghz128_m2e27": bench_ghz128(S, C)}
     if rank == 0:
         line = {
@@ -959,7 +1102,8 @@ def run_ours(args, world, rank, local):
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": desc, "n": args.n, "depth": args.depth, "seed": args.seed, "state": "complex64",
-                       "mode": mode, "launches_per_step": launches_per_step, "parallelism": f"replicas x{world}",
+                       "mode": mode, "autotune": tuning, "launches_per_step": launches_per_step,
+                       "parallelism": f"replicas x{world}",
                        "l2": "state (32 GiB) larger than L2, no flush"},
             "hbm_gbs": gbs, "layers_per_s": args.depth * args.steps * world / t,
             "accuracy": {"roundtrip_1_minus_fidelity": roundtrip_infidelity, "roundtrip_norm_minus_1": norm_drift,
@@ -972,6 +1116,9 @@ def run_ours(args, world, rank, local):
 
 def main():
     args = parse_args()
+    if args.profile_case:
+        run_profile_case(args.profile_case)
+        return
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, world, rank)

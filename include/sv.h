@@ -53,6 +53,7 @@ extern "C" {
 
 typedef struct sv_state *sv_handle;
 typedef struct sv_plan_s *sv_plan;
+typedef struct sv_batch_s *sv_batch;
 
 typedef enum { SV_C64 = 0, SV_C128 = 1, SV_ENC2B = 2 } sv_dtype;
 
@@ -73,9 +74,17 @@ typedef enum {
     SV_MODE_PERGATE = 0,     /* one HBM pass per gate (Eq. 1 per gate) */
     SV_MODE_TILED = 1,       /* many gates per HBM pass: 2^13-amplitude tiles in
                                 shared memory, one compiled kernel per pass */
-    SV_MODE_FUSED = 2        /* gates fused into dense k-qubit blocks (k = 3..6
+    SV_MODE_FUSED = 2,       /* gates fused into dense k-qubit blocks (k = 3..6
                                 chosen by the planner), one HBM pass per block on
                                 the tensor cores */
+    SV_MODE_AUTO = 3         /* measured choice: sv_plan_create plans every
+                                candidate (tiled with each register-bit, CTA and
+                                HBM-I/O configuration of the generator; fused
+                                with k = 3..6; per-gate where no tile fits),
+                                times each on a scratch state of the handle's
+                                size and keeps the fastest; the choice is
+                                remembered per device, n, dtype and circuit
+                                (sv_plan_tuning reports it) */
 } sv_mode;
 
 /* ---- lifecycle --------------------------------------------------------- */
@@ -144,13 +153,18 @@ sv_status sv_apply_fused(sv_handle h, int k, const int *qubits, const double *U)
  * "CP 2 5 0.785", "U 4 <8 doubles>", see the package documentation) on the
  * handle's current state, with one of the sv_mode strategies.  All modes
  * compute the same product of gate matrices (Sec. 2); they differ in how
- * many HBM passes they make.  SV_ENC2B supports SV_MODE_PERGATE only.
- * Errors: SV_ERR_PARSE, SV_ERR_ARG (qubit range), SV_ERR_DTYPE. */
+ * many HBM passes they make.  SV_ENC2B supports SV_MODE_PERGATE (and
+ * SV_MODE_AUTO, which then has only that candidate).  Errors: SV_ERR_PARSE,
+ * SV_ERR_ARG (qubit range), SV_ERR_DTYPE. */
 sv_status sv_run_circuit(sv_handle h, const char *text, int mode);
 
 /* Plan a circuit once (parse, classify gates, group them into HBM passes,
  * upload the pass programs) and execute it many times.  The plan is bound
- * to the handle and must be freed before it. */
+ * to the handle and must be freed before it.  SV_MODE_AUTO times its
+ * candidates here, on a scratch state that it cudaMallocs and frees (the
+ * handle's state is not touched); without room for one it takes the tiled
+ * plan.  Its first tuning of a large circuit takes seconds (every candidate
+ * is compiled and run three times). */
 sv_status sv_plan_create(sv_handle h, const char *text, int mode, sv_plan *out);
 /* Execute a plan on the handle's stream (asynchronous).  The first execution
  * launches the kernels one by one; the second captures them into a CUDA graph
@@ -169,10 +183,32 @@ sv_status sv_plan_info(sv_plan p, int64_t *gates, int64_t *passes, double *bytes
 /* Per-launch timing hook: execute the plan and record event[i] (caller-
  * created cudaEvent_t) before launch i and event[passes] after the last. */
 sv_status sv_plan_execute_timed(sv_plan p, void *const *events, int64_t n_events);
+/* The autotuner's record of an SV_MODE_AUTO plan as JSON text: each
+ * candidate strategy with its measured ms per execution and the chosen one
+ * ({"timed": false, ...} when the choice was remembered from an earlier
+ * tuning or no scratch state fitted); "" for other modes.  buf (cap bytes,
+ * NUL-terminated, may be NULL), *len = the full length. */
+sv_status sv_plan_tuning(sv_plan p, char *buf, size_t cap, size_t *len);
 sv_status sv_plan_free(sv_plan p);
 /* Launch i of a plan (0 <= i < passes): the name of the kernel it runs and
  * the algorithmic bytes it moves.  *kernel points to a static string. */
 sv_status sv_plan_launch_info(sv_plan p, int64_t i, const char **kernel, double *bytes);
+
+/* Launch i of a plan: for a compiled tile pass, the FP32 lane operations per
+ * amplitude its gates need at least (2 per structured butterfly such as H,
+ * SX, SY; 1 per T-type phase; 4 per other complex phase; 8 per dense 2x2;
+ * times the fraction of amplitudes its controls leave; sign flips and X
+ * free) and its register segments (shared-memory transpositions + 1); 0 and
+ * 0 for other launches.  Either pointer may be NULL. */
+sv_status sv_plan_launch_stats(sv_plan p, int64_t i, double *fp32_ops_per_amplitude, int64_t *segments);
+
+/* Host only (no GPU needed): the generated CUDA source of pass `pass` of the
+ * SV_MODE_TILED plan of a circuit (what a plan compiles with NVRTC), into
+ * buf (cap bytes, NUL-terminated, truncated if short; buf may be NULL);
+ * *len receives the full length.  Errors: SV_ERR_PARSE, SV_ERR_ARG (pass out
+ * of range), SV_ERR_UNSUPPORTED (n below one tile). */
+sv_status sv_plan_pass_source(const char *text, int n, sv_dtype dt, int64_t pass, char *buf, size_t cap,
+                              size_t *len);
 
 /* Host only (no GPU needed): plan a circuit for SV_MODE_TILED and report its
  * gate count, HBM passes and register segments; with compile != 0 also
@@ -182,6 +218,32 @@ sv_status sv_plan_launch_info(sv_plan p, int64_t i, const char **kernel, double 
  * SV_ERR_CUDA (compile failure). */
 sv_status sv_plan_stats(const char *text, int n, sv_dtype dt, int compile, int64_t *gates, int64_t *passes,
                         int64_t *segments);
+
+/* ---- batches of independent circuits ------------------------------------------ */
+
+/* A batch of count independent circuits, member k = texts[k] on its own
+ * state handles[k] (SV_C64 or SV_C128, sizes may differ, no state shared,
+ * all on one device).  Each member is planned as in SV_MODE_TILED (per-gate
+ * updates below one tile).  sv_batch_execute runs all members together: on
+ * its first call with direct launches, then as one CUDA graph in which each
+ * member is an independent chain of its launches, so passes of different
+ * members run concurrently and small states no longer leave the GPU idle
+ * (Sec. 4: independent terms; the same holds for unrelated circuits).  The
+ * batch runs on a private stream that every member handle's stream is
+ * joined to by events before and after, so work queued on them stays in
+ * order (sv_batch_execute is asynchronous like a gate call).  Ownership: the batch holds one plan per member (the handles must
+ * outlive it; free the batch first).  Errors: SV_ERR_ARG (NULL, count < 1 or
+ * > 4096, a state shared by two members, mixed devices), SV_ERR_DTYPE
+ * (SV_ENC2B), SV_ERR_PARSE, plus those of sv_plan_create. */
+sv_status sv_batch_create(const sv_handle *handles, const char *const *texts, int count, sv_batch *out);
+/* Run every member's circuit once on its current state (asynchronous). */
+sv_status sv_batch_execute(sv_batch b);
+/* Gates of all members, their launches per execution, algorithmic bytes,
+ * and whether executions now replay the graph (any pointer may be NULL). */
+sv_status sv_batch_info(sv_batch b, int64_t *gates, int64_t *launches, double *bytes, int *uses_graph);
+sv_status sv_batch_free(sv_batch b);
+/* Create, execute once and free. */
+sv_status sv_run_batch(const sv_handle *handles, const char *const *texts, int count);
 
 /* ---- two-byte encoding (Sec. 1 and Sec. 3) ---------------------------------- */
 
@@ -277,6 +339,20 @@ sv_status sv_cut_amplitudes(const char *text, int n, uint64_t maskA, int form, s
 sv_status sv_cut_amplitudes_part(const char *text, int n, uint64_t maskA, int form, uint64_t part, int nparts_log2,
                                  size_t m, const uint64_t *z, double *out, int *n_cut_out, void *stream);
 
+/* The Eq. 3 sum over the branches of several parts at once: the parts
+ * parts[0..nlist-1] of 2^nparts_log2 (each < 2^nparts_log2, none repeated,
+ * 1 <= nlist <= 2^nparts_log2), as sv_cut_amplitudes_part would give them
+ * one by one, added in FP64 on the device (Sec. 4: the terms are
+ * independent, so a process or GPU sums its share and one reduction over
+ * them all gives <z|C|0>).  The parts run one after another on the same
+ * device buffers, so memory is that of one part.  A rank r of W processes
+ * takes nparts_log2 = ceil(log2 W) and the parts p with p mod W = r.  Other
+ * arguments and errors as sv_cut_amplitudes_part; SV_ERR_ARG for a bad
+ * list. */
+sv_status sv_cut_amplitudes_parts(const char *text, int n, uint64_t maskA, int form, int nparts_log2, size_t nlist,
+                                  const uint64_t *parts, size_t m, const uint64_t *z, double *out, int *n_cut_out,
+                                  void *stream);
+
 /* Eq. 3 over P partitions (Sec. 4: the sum over s of products of P
  * circuits that each act on one partition, with memory bound by the largest
  * partition's dimension).  part_of[q] in 0..P-1 gives the partition of each
@@ -291,6 +367,13 @@ sv_status sv_cut_amplitudes_part(const char *text, int n, uint64_t maskA, int fo
 sv_status sv_cut_amplitudes_multi(const char *text, int n, const uint8_t *part_of, int P, int form, uint64_t part,
                                   int nparts_log2, size_t m, const uint64_t *z, double *out, int *n_cut_out,
                                   void *stream);
+
+/* sv_cut_amplitudes_parts over P partitions: the listed branch parts of
+ * sv_cut_amplitudes_multi summed in FP64 on the device.  Arguments and
+ * errors as sv_cut_amplitudes_multi and sv_cut_amplitudes_parts. */
+sv_status sv_cut_amplitudes_multi_parts(const char *text, int n, const uint8_t *part_of, int P, int form,
+                                        int nparts_log2, size_t nlist, const uint64_t *parts, size_t m,
+                                        const uint64_t *z, double *out, int *n_cut_out, void *stream);
 
 /* ---- host-only helpers (no GPU needed) -------------------------------------------- */
 

@@ -52,6 +52,7 @@ constexpr int kMaxCutQubits = 128;  // qubits of the circuit
 
 struct CutSumArgs {
     int P, Sv, nwords;
+    int accumulate;  // add to out (the sum over several branch parts) instead of writing it
     uint64_t m;
     double w;
     const float2 *vec[kMaxParts];
@@ -94,7 +95,15 @@ __global__ void k_cut_sum(const uint64_t *__restrict__ z, const CutSumArgs a, do
             re += __shfl_xor_sync(0xffffffffu, re, o);
             im += __shfl_xor_sync(0xffffffffu, im, o);
         }
-        if (lane == 0) out[j] = make_double2(a.w * re, a.w * im);
+        if (lane == 0) {
+            double2 v = make_double2(a.w * re, a.w * im);
+            if (a.accumulate) {
+                const double2 o = out[j];
+                v.x += o.x;
+                v.y += o.y;
+            }
+            out[j] = v;
+        }
     }
 }
 
@@ -128,6 +137,15 @@ void append_lowered(const Instr &ins, std::vector<PGate> *out) {
     out->insert(out->end(), g.begin(), g.end());
 }
 
+// One step of a partition's simulation: a stage of compiled tiled passes
+// over the low 2^nrun amplitudes, or (branch-prefix sharing) a fork that
+// copies the live 2^live amplitudes to the slots above them.
+struct HalfStep {
+    std::vector<void *> fns;  // compiled passes of a stage; empty for a fork
+    int nrun = 0, rb = 0;
+    int live = -1;            // fork: live qubits before the copy
+};
+
 struct Half {            // one partition
     int nlocal = 0;     // qubits of the partition
     int nbits = 0;      // batched branch bits of the cuts touching it
@@ -136,29 +154,23 @@ struct Half {            // one partition
     std::vector<int> qubits;   // circuit qubit of local qubit i
     std::vector<int> cutbits;  // batched branch bit of partition bit j
     float2 *d = nullptr;
+    bool init_all = false;     // every branch starts at its own |0> (no prefix sharing)
+    std::vector<HalfStep> steps;
 };
 
-// Compile and run `gates` as tiled passes over the low 2^nrun amplitudes.
-sv_status run_stage(Half &h, cudaStream_t st, const std::vector<PGate> &gates, int nrun) {
+// Plan and compile `gates` as tiled passes over the low 2^nrun amplitudes.
+sv_status plan_stage(std::vector<HalfStep> *steps, const std::vector<PGate> &gates, int nrun) {
     if (gates.empty()) return SV_OK;
     TilePlan<float> tp;
-    sv_status s = plan_tiles<float>(gates, nrun, TileConfig{kTileM64, tile_rb64(), tile_low64(), true}, &tp);
+    sv_status s = plan_tiles<float>(gates, nrun, tile_config64(), &tp);
     if (s) return s;
-    std::vector<void *> fns;
-    s = jit_tile_plan(tp, &fns);
+    HalfStep st;
+    s = jit_tile_plan(tp, &st.fns);
     if (s) return s;
-    sv_state tmp;
-    tmp.n = nrun;
-    tmp.dt = SV_C64;
-    tmp.data = h.d;
-    tmp.stream = st;
-    SV_CUDA_TRY(cudaGetDevice(&tmp.device));
-    for (void *fn : fns) {
-        s = check_launch(launch_jit_pass(&tmp, fn, nrun, tp.rb), "branch pass");
-        if (s) break;
-    }
-    tmp.data = nullptr;
-    return s;
+    st.nrun = nrun;
+    st.rb = tp.rb;
+    steps->push_back(std::move(st));
+    return SV_OK;
 }
 
 // Branch-prefix sharing (on unless SV_CUT_PREFIX=0): the gates before the
@@ -175,41 +187,71 @@ bool prefix_sharing() {
     return !(e && e[0] == '0');
 }
 
-sv_status run_half(Half &h, cudaStream_t st, int S) {
-    SV_CUDA_TRY(cudaMemsetAsync(h.d, 0, sizeof(float2) << h.nq, st));
-    if (!prefix_sharing()) {
-        k_branch_init<<<64, 256, 0, st>>>(h.d, h.nlocal, S);
-        sv_status s = check_launch(cudaGetLastError(), "k_branch_init");
-        return s ? s : run_stage(h, st, h.gates, h.nq);
-    }
-    k_branch_init<<<1, 32, 0, st>>>(h.d, h.nlocal, 0);
-    sv_status s = check_launch(cudaGetLastError(), "k_branch_init");
-    if (s) return s;
+// The schedule of a partition: planned and compiled once, then run for every
+// branch part (the fixed branch bits of a part are launch parameters).
+sv_status plan_half(Half &h, int S) {
+    h.steps.clear();
+    h.init_all = !prefix_sharing();
+    if (h.init_all) return plan_stage(&h.steps, h.gates, h.nq);
     int live = h.nlocal;  // live amplitudes: 2^live
     std::vector<PGate> stage;
     auto fork = [&]() -> sv_status {
-        s = run_stage(h, st, stage, live > kTileM64 ? live : kTileM64);
+        sv_status s = plan_stage(&h.steps, stage, live > kTileM64 ? live : kTileM64);
         stage.clear();
         if (s) return s;
-        const size_t bytes = sizeof(float2) << live;
-        SV_CUDA_TRY(cudaMemcpyAsync(reinterpret_cast<char *>(h.d) + bytes, h.d, bytes, cudaMemcpyDeviceToDevice, st));
-        ++live;
+        HalfStep f;
+        f.live = live++;
+        h.steps.push_back(f);
         return SV_OK;
     };
     for (const PGate &g : h.gates) {
-        // branch bits are only ever conditions of diagonal gates
-        const uint64_t branch = g.kind == 1 ? (g.cmask >> h.nlocal) : 0;
+        // batched branch bits are only ever conditions of diagonal gates
+        const uint64_t branch = g.kind == 1 ? ((g.cmask & kQubitBits) >> h.nlocal) : 0;
         while (branch >> (live - h.nlocal)) {
-            s = fork();
+            sv_status s = fork();
             if (s) return s;
         }
         stage.push_back(g);
     }
     while (live < h.nlocal + S) {  // every branch bit has operators; kept for the layout
-        s = fork();
+        sv_status s = fork();
         if (s) return s;
     }
-    return run_stage(h, st, stage, h.nq);
+    return plan_stage(&h.steps, stage, h.nq);
+}
+
+// Run a partition's schedule for the branch part whose fixed bits are param.
+sv_status exec_half(Half &h, cudaStream_t st, int S, uint64_t param) {
+    SV_CUDA_TRY(cudaMemsetAsync(h.d, 0, sizeof(float2) << h.nq, st));
+    if (h.init_all) k_branch_init<<<64, 256, 0, st>>>(h.d, h.nlocal, S);
+    else k_branch_init<<<1, 32, 0, st>>>(h.d, h.nlocal, 0);
+    sv_status s = check_launch(cudaGetLastError(), "k_branch_init");
+    if (s) return s;
+    sv_state tmp;
+    tmp.dt = SV_C64;
+    tmp.data = h.d;
+    tmp.stream = st;
+    SV_CUDA_TRY(cudaGetDevice(&tmp.device));
+    for (const HalfStep &step : h.steps) {
+        if (step.fns.empty()) {
+            const size_t bytes = sizeof(float2) << step.live;
+            const cudaError_t e =
+                cudaMemcpyAsync(reinterpret_cast<char *>(h.d) + bytes, h.d, bytes, cudaMemcpyDeviceToDevice, st);
+            if (e != cudaSuccess) {
+                s = cuda_status(e, "cudaMemcpyAsync (branch fork)");
+                break;
+            }
+            continue;
+        }
+        tmp.n = step.nrun;
+        for (void *fn : step.fns) {
+            s = check_launch(launch_jit_pass(&tmp, fn, step.nrun, step.rb, param), "branch pass");
+            if (s) break;
+        }
+        if (s) break;
+    }
+    tmp.data = nullptr;
+    return s;
 }
 
 }  // namespace
@@ -217,13 +259,16 @@ sv_status run_half(Half &h, cudaStream_t st, int S) {
 
 using namespace sv;
 
-// Sum over the branches s with s mod 2^plog == part (plog = 0: all of them).
-// The low plog branch bits are then fixed: their branch operators are plain
-// diagonal gates on the partitions' qubits, and only the other S - plog bits
-// are batched.  z: m bit strings of nwords 64-bit words (qubit q is bit q % 64
-// of word q / 64).
-static sv_status cut_impl(const char *text, int n, const uint8_t *part_of, int P, int form, uint64_t part, int plog,
-                          size_t m, const uint64_t *z, int nwords, double *out, int *n_cut_out, void *stream) {
+// Sum over the branches s with s mod 2^plog in the list plist (plog = 0,
+// plist = {0}: all of them).  For each listed part the low plog branch bits
+// are fixed: their branch operators are plain diagonal gates on the
+// partitions' qubits, and only the other S - plog bits are batched; the parts
+// run one after another on the same device buffers and their sums add up in
+// FP64 on the device.  z: m bit strings of nwords 64-bit words (qubit q is bit
+// q % 64 of word q / 64).
+static sv_status cut_impl(const char *text, int n, const uint8_t *part_of, int P, int form, const uint64_t *plist,
+                          size_t nlist, int plog, size_t m, const uint64_t *z, int nwords, double *out, int *n_cut_out,
+                          void *stream) {
     if (n < 2 || n > kMaxCutQubits || P < 2 || P > kMaxParts || !part_of || (form != 0 && form != 1) ||
         nwords != (n + 63) / 64 || (m > 0 && (!z || !out))) {
         set_error("bad arguments (n=%d, P=%d, form=%d, nwords=%d)", n, P, form, nwords);
@@ -269,19 +314,31 @@ static sv_status cut_impl(const char *text, int n, const uint8_t *part_of, int P
         }
         ++S;
     }
+    if (n_cut_out) *n_cut_out = S;
     if (S - plog > 16) {
         set_error("%d decomposed gates, %d of them batched (at most 16)", S, S - plog);
         return SV_ERR_UNSUPPORTED;
     }
     const int Svar = S > plog ? S - plog : 0;  // batched branch bits
     if (n_cut_out) *n_cut_out = S;
-    if (S < 64 && (part >> S) != 0) {  // no branch has these low bits
+    // the listed parts that hold branches (a part whose low bits exceed every
+    // branch index has none)
+    std::vector<uint64_t> todo;
+    for (size_t i = 0; i < nlist; ++i)
+        if (!(S < 64 && (plist[i] >> S) != 0)) todo.push_back(plist[i]);
+    if (todo.empty()) {
         for (size_t j = 0; j < 2 * m; ++j) out[j] = 0.0;
         return SV_OK;
     }
     // branch operators: a Z-basis projector (or Eq. 2 phase) on the first
     // qubit's partition, the phase on the second's, conditioned on the cut's
     // branch bit, which each partition holds above its own qubits
+    auto build = [&]() -> sv_status {
+    for (int p = 0; p < P; ++p) {
+        parts[p].gates.clear();
+        parts[p].cutbits.clear();
+        parts[p].nbits = 0;
+    }
     int k = 0;
     for (const Instr &ins0 : c.instrs) {
         Instr ins = ins0;
@@ -302,9 +359,10 @@ static sv_status cut_impl(const char *text, int n, const uint8_t *part_of, int P
             append_lowered(h, &B.gates);
         }
         const uint64_t la = uint64_t(1) << loc[qa], lb = uint64_t(1) << loc[qb];
+        // a fixed branch bit (one of the low plog) is a launch parameter bit:
+        // the same compiled passes serve every part
         const bool fixed = k < plog;
-        const int sfix = int((part >> k) & 1);
-        uint64_t ka = 0, kb = 0;
+        uint64_t ka = uint64_t(1) << (kParamBit0 + k), kb = ka;
         if (!fixed) {
             if (A.nbits >= kMaxCutBits || B.nbits >= kMaxCutBits) {
                 set_error("a partition touches more than %d batched cuts", kMaxCutBits);
@@ -316,17 +374,11 @@ static sv_status cut_impl(const char *text, int n, const uint8_t *part_of, int P
             kb = uint64_t(1) << (B.nlocal + B.nbits++);
         }
         if (form == 0) {
-            if (fixed) {
-                A.gates.push_back(phase_gate(la, sfix ? 0 : la, 0.0));  // keep bit a == s_k
-                if (sfix) B.gates.push_back(phase_gate(lb, lb, std::polar(1.0, theta)));
-            } else {
-                A.gates.push_back(phase_gate(la | ka, la, 0.0));  // bit a = 1, s_k = 0: P0 removes it
-                A.gates.push_back(phase_gate(la | ka, ka, 0.0));  // bit a = 0, s_k = 1: P1 removes it
-                B.gates.push_back(phase_gate(lb | kb, lb | kb, std::polar(1.0, theta)));
-            }
+            A.gates.push_back(phase_gate(la | ka, la, 0.0));  // bit a = 1, s_k = 0: P0 removes it
+            A.gates.push_back(phase_gate(la | ka, ka, 0.0));  // bit a = 0, s_k = 1: P1 removes it
+            B.gates.push_back(phase_gate(lb | kb, lb | kb, std::polar(1.0, theta)));
         } else {
             for (int sb = 0; sb < 2; ++sb) {
-                if (fixed && sb != sfix) continue;
                 cd d[2];
                 eq2_diag(sb, d);
                 const uint64_t sva = sb ? ka : 0, svb = sb ? kb : 0;
@@ -347,6 +399,10 @@ static sv_status cut_impl(const char *text, int n, const uint8_t *part_of, int P
             return SV_ERR_UNSUPPORTED;
         }
     }
+    return SV_OK;
+    };
+    s = build();
+    if (s) return s;
     if (m == 0) return SV_OK;
 
     // device memory: the batched vectors + bit strings + results
@@ -381,13 +437,19 @@ static sv_status cut_impl(const char *text, int n, const uint8_t *part_of, int P
         release();
         return cuda_status(e, "cudaMalloc (decomposition)");
     }
-    for (int p = 0; p < P && s == SV_OK; ++p) s = run_half(parts[p], st, parts[p].nbits);
     if (s == SV_OK) {
         e = cudaMemcpyAsync(dz, z, bytesZ, cudaMemcpyHostToDevice, st);
         if (e != cudaSuccess) s = cuda_status(e, "cudaMemcpyAsync");
     }
-    if (s == SV_OK) {
+    for (int p = 0; p < P && s == SV_OK; ++p) s = plan_half(parts[p], parts[p].nbits);
+    for (size_t ip = 0; ip < todo.size() && s == SV_OK; ++ip) {
+        // every part runs the same compiled passes (its fixed branch bits are
+        // the launch parameter) on the same buffers; the stream orders its
+        // halves after the previous part's sum
+        for (int p = 0; p < P && s == SV_OK; ++p) s = exec_half(parts[p], st, parts[p].nbits, todo[ip]);
+        if (s != SV_OK) break;
         CutSumArgs a{};
+        a.accumulate = ip > 0;
         a.P = P;
         a.Sv = Svar;
         a.nwords = nwords;
@@ -414,8 +476,8 @@ static sv_status cut_impl(const char *text, int n, const uint8_t *part_of, int P
 }
 
 // Two partitions given by a mask (partition 0 = the mask's qubits).
-static sv_status cut_mask(const char *text, int n, uint64_t maskA, int form, uint64_t part, int plog, size_t m,
-                          const uint64_t *z, double *out, int *n_cut_out, void *stream) {
+static sv_status cut_mask(const char *text, int n, uint64_t maskA, int form, const uint64_t *plist, size_t nlist,
+                          int plog, size_t m, const uint64_t *z, double *out, int *n_cut_out, void *stream) {
     if (n < 2 || n > 64) {
         set_error("n = %d outside 2..64 (sv_cut_amplitudes_multi takes up to %d qubits)", n, kMaxCutQubits);
         return SV_ERR_ARG;
@@ -427,12 +489,47 @@ static sv_status cut_mask(const char *text, int n, uint64_t maskA, int form, uin
     }
     uint8_t part_of[64];
     for (int q = 0; q < n; ++q) part_of[q] = (maskA >> q & 1) ? 0 : 1;
-    return cut_impl(text, n, part_of, 2, form, part, plog, m, z, 1, out, n_cut_out, stream);
+    return cut_impl(text, n, part_of, 2, form, plist, nlist, plog, m, z, 1, out, n_cut_out, stream);
+}
+
+// A list of branch parts: each < 2^plog and none repeated.
+static sv_status check_parts(const uint64_t *plist, size_t nlist, int plog) {
+    if (plog < 0 || plog > 16 || nlist == 0 || nlist > (size_t(1) << plog) || !plist) {
+        set_error("bad part list (%zu parts of 2^%d)", nlist, plog);
+        return SV_ERR_ARG;
+    }
+    std::vector<char> seen(size_t(1) << plog, 0);
+    for (size_t i = 0; i < nlist; ++i) {
+        if ((plist[i] >> plog) != 0 || seen[plist[i]]) {
+            set_error("part %llu at position %zu is out of range or repeated (2^%d parts)",
+                      (unsigned long long)plist[i], i, plog);
+            return SV_ERR_ARG;
+        }
+        seen[plist[i]] = 1;
+    }
+    return SV_OK;
 }
 
 extern "C" sv_status sv_cut_amplitudes(const char *text, int n, uint64_t maskA, int form, size_t m, const uint64_t *z,
                                        double *out, int *n_cut_out, void *stream) {
-    return cut_mask(text, n, maskA, form, 0, 0, m, z, out, n_cut_out, stream);
+    const uint64_t all = 0;
+    return cut_mask(text, n, maskA, form, &all, 1, 0, m, z, out, n_cut_out, stream);
+}
+
+extern "C" sv_status sv_cut_amplitudes_parts(const char *text, int n, uint64_t maskA, int form, int nparts_log2,
+                                             size_t nlist, const uint64_t *parts, size_t m, const uint64_t *z,
+                                             double *out, int *n_cut_out, void *stream) {
+    sv_status s = check_parts(parts, nlist, nparts_log2);
+    return s ? s : cut_mask(text, n, maskA, form, parts, nlist, nparts_log2, m, z, out, n_cut_out, stream);
+}
+
+extern "C" sv_status sv_cut_amplitudes_multi_parts(const char *text, int n, const uint8_t *part_of, int P, int form,
+                                                   int nparts_log2, size_t nlist, const uint64_t *parts, size_t m,
+                                                   const uint64_t *z, double *out, int *n_cut_out, void *stream) {
+    sv_status s = check_parts(parts, nlist, nparts_log2);
+    return s ? s
+             : cut_impl(text, n, part_of, P, form, parts, nlist, nparts_log2, m, z, (n + 63) / 64, out, n_cut_out,
+                        stream);
 }
 
 extern "C" sv_status sv_cut_amplitudes_part(const char *text, int n, uint64_t maskA, int form, uint64_t part,
@@ -442,7 +539,7 @@ extern "C" sv_status sv_cut_amplitudes_part(const char *text, int n, uint64_t ma
         set_error("bad part %llu of 2^%d", (unsigned long long)part, nparts_log2);
         return SV_ERR_ARG;
     }
-    return cut_mask(text, n, maskA, form, part, nparts_log2, m, z, out, n_cut_out, stream);
+    return cut_mask(text, n, maskA, form, &part, 1, nparts_log2, m, z, out, n_cut_out, stream);
 }
 
 extern "C" sv_status sv_cut_amplitudes_multi(const char *text, int n, const uint8_t *part_of, int P, int form,
@@ -452,5 +549,5 @@ extern "C" sv_status sv_cut_amplitudes_multi(const char *text, int n, const uint
         set_error("bad part %llu of 2^%d", (unsigned long long)part, nparts_log2);
         return SV_ERR_ARG;
     }
-    return cut_impl(text, n, part_of, P, form, part, nparts_log2, m, z, (n + 63) / 64, out, n_cut_out, stream);
+    return cut_impl(text, n, part_of, P, form, &part, 1, nparts_log2, m, z, (n + 63) / 64, out, n_cut_out, stream);
 }

@@ -4,6 +4,8 @@
 
 #include <mutex>
 #include <unordered_map>
+#include <cstring>
+
 #include "plan.h"
 
 namespace sv {
@@ -45,13 +47,15 @@ void destroy_plan(sv_plan_s *p) {
     delete p;
 }
 
-// Fused mode: blocks of at most k qubits; the autotuner takes the k in 3..6
-// with the fewest blocks (each block is one HBM pass; ties to the smaller k).
-sv_status build_fused_plan(sv_state *h, const Circuit &c, sv_plan_s *p) {
+// Fused mode: blocks of at most k qubits; without a measured choice
+// (kfix = 0) the k in 3..6 with the fewest blocks (each block is one HBM
+// pass; ties to the smaller k).
+sv_status build_fused_plan(sv_state *h, const Circuit &c, sv_plan_s *p, int kfix = 0) {
     std::vector<FusedBlock> best;
     int bestk = 0;
-    const int kmin = h->n < 3 ? h->n : 3;
-    for (int k = kmin; k <= kMaxFusedQubits && k <= h->n; ++k) {
+    const int kmin = kfix ? kfix : (h->n < 3 ? h->n : 3);
+    const int kmax = kfix ? kfix : kMaxFusedQubits;
+    for (int k = kmin; k <= kmax && k <= h->n; ++k) {
         std::vector<FusedBlock> b = fuse_blocks(c, k);
         if (bestk == 0 || b.size() < best.size()) {
             best.swap(b);
@@ -79,25 +83,30 @@ sv_status build_fused_plan(sv_state *h, const Circuit &c, sv_plan_s *p) {
 
 template <typename R>
 sv_status upload_tile_plan(sv_plan_s *p, const TilePlan<R> &tp) {
+    p->tile_lane_ops = tp.lane_ops;
+    p->tile_nseg = tp.nseg;
     sv_status s = jit_tile_plan(tp, &p->tfns);
     if (s) return s;
     p->tile_rb = tp.rb;
     const double pass_bytes = 2.0 * double(uint64_t(1) << p->h->n) * (p->h->dt == SV_C64 ? 8.0 : 16.0);
     for (size_t i = 0; i < tp.passes.size(); ++i) {
-        p->launches.push_back(PlanLaunch{1, int(i), pass_bytes});  // compiled pass i
+        PlanLaunch l{1, int(i), pass_bytes};  // compiled pass i
+        l.lane_ops = tp.lane_ops[i];
+        l.segments = tp.nseg[i];
+        p->launches.push_back(l);
         p->bytes += pass_bytes;
     }
     return SV_OK;
 }
 
-sv_status build_tile_plan(sv_state *h, const Circuit &c, sv_plan_s *p) {
+sv_status build_tile_plan(sv_state *h, const Circuit &c, sv_plan_s *p, const TileConfig &cfg) {
     if (h->dt == SV_C64) {
         TilePlan<float> tp;
-        sv_status s = plan_tiles<float>(c, h->n, TileConfig{kTileM64, tile_rb64(), tile_low64(), true}, &tp);
+        sv_status s = plan_tiles<float>(c, h->n, cfg, &tp);
         return s ? s : upload_tile_plan(p, tp);
     }
     TilePlan<double> tp;
-    sv_status s = plan_tiles<double>(c, h->n, TileConfig{kTileM128, kTileRB128, kTileLow128, false}, &tp);
+    sv_status s = plan_tiles<double>(c, h->n, tile_config128(), &tp);
     return s ? s : upload_tile_plan(p, tp);
 }
 
@@ -135,21 +144,288 @@ namespace {
 
 // Tiled plans by circuit text: a repeated circuit skips parsing, planning and
 // code generation (its compiled passes stay loaded for the process).  The key
-// holds everything the plan depends on: device, dtype, qubit count, planner
-// and code-generation settings, and the text.
+// holds everything the plan depends on: device, dtype, qubit count, tile
+// configuration, planner and code-generation settings, and the text.
 struct TileCacheEntry {
     std::vector<void *> fns;
     int rb = 0;
     int64_t gates = 0;
+    std::vector<double> lane_ops;
+    std::vector<int> nseg;
 };
 std::mutex g_tile_cache_mu;
 std::unordered_map<std::string, TileCacheEntry> g_tile_cache;
 constexpr size_t kTileCacheMax = 64;
 
-std::string tile_cache_key(const sv_state *h, const char *text) {
-    return std::to_string(h->device) + "|" + std::to_string(int(h->dt)) + "|" + std::to_string(h->n) + "|rb=" +
-           std::to_string(tile_rb64()) + ",low=" + std::to_string(tile_low64()) + ",look=" +
-           std::to_string(plan_lookahead_width()) + "," + tile_codegen_key() + "|" + text;
+std::string tile_cache_key(const sv_state *h, const TileConfig &cfg, const char *text) {
+    return std::to_string(h->device) + "|" + std::to_string(int(h->dt)) + "|" + std::to_string(h->n) + "|" +
+           tile_config_name(cfg) + ",look=" + std::to_string(plan_lookahead_width()) + "," + tile_codegen_key() +
+           "|" + text;
+}
+
+// One candidate execution strategy: a mode, and for the tiled mode the tile
+// configuration, for the fused mode the block width (0 = fewest blocks).
+struct Strategy {
+    int mode = SV_MODE_TILED;
+    TileConfig cfg{};
+    int k = 0;
+    std::string name() const {
+        if (mode == SV_MODE_TILED) return "tiled " + tile_config_name(cfg);
+        if (mode == SV_MODE_FUSED) return "fused k=" + std::to_string(k);
+        return "pergate";
+    }
+};
+
+TileConfig default_config(const sv_state *h) { return h->dt == SV_C64 ? tile_config64() : tile_config128(); }
+
+// Build the plan of one strategy for the handle (text already parsed into c).
+sv_status create_plan(sv_state *h, const char *text, const Circuit &c, const Strategy &st, sv_plan_s **out) {
+    *out = nullptr;
+    const int tile_m = h->dt == SV_C64 ? kTileM64 : kTileM128;
+    const bool tiled = st.mode == SV_MODE_TILED && h->n >= tile_m;
+    std::string key;
+    if (tiled && text) {
+        key = tile_cache_key(h, st.cfg, text);
+        std::lock_guard<std::mutex> lock(g_tile_cache_mu);
+        auto it = g_tile_cache.find(key);
+        if (it != g_tile_cache.end()) {
+            sv_plan_s *p = new sv_plan_s;
+            p->h = h;
+            p->mode = st.mode;
+            p->gates = it->second.gates;
+            p->tfns = it->second.fns;
+            p->tile_rb = it->second.rb;
+            p->tile_lane_ops = it->second.lane_ops;
+            p->tile_nseg = it->second.nseg;
+            const double pass_bytes = 2.0 * double(uint64_t(1) << h->n) * (h->dt == SV_C64 ? 8.0 : 16.0);
+            for (size_t i = 0; i < p->tfns.size(); ++i) {
+                PlanLaunch l{1, int(i), pass_bytes};
+                l.lane_ops = i < p->tile_lane_ops.size() ? p->tile_lane_ops[i] : 0.0;
+                l.segments = i < p->tile_nseg.size() ? p->tile_nseg[i] : 0;
+                p->launches.push_back(l);
+                p->bytes += pass_bytes;
+            }
+            *out = p;
+            return SV_OK;
+        }
+    }
+    sv_plan_s *p = new sv_plan_s;
+    p->h = h;
+    p->mode = st.mode;
+    p->gates = int64_t(c.instrs.size());
+    sv_status s = SV_OK;
+    if (st.mode == SV_MODE_FUSED) {
+        s = build_fused_plan(h, c, p, st.k);
+    } else if (st.mode == SV_MODE_PERGATE || h->n < tile_m) {
+        // per-gate updates (also the tiled mode's path for states smaller than one tile)
+        p->pergate = lower_to_gate1(c);
+        for (size_t i = 0; i < p->pergate.size(); ++i) {
+            const double b = gate1_bytes(h, p->pergate[i]);
+            p->launches.push_back(PlanLaunch{0, int(i), b});
+            p->bytes += b;
+        }
+    } else {
+        s = build_tile_plan(h, c, p, st.cfg);
+        if (!s && !key.empty()) {
+            std::lock_guard<std::mutex> lock(g_tile_cache_mu);
+            if (g_tile_cache.size() >= kTileCacheMax) g_tile_cache.clear();
+            g_tile_cache[key] = TileCacheEntry{p->tfns, p->tile_rb, p->gates, p->tile_lane_ops, p->tile_nseg};
+        }
+    }
+    if (s) {
+        destroy_plan(p);
+        return s;
+    }
+    *out = p;
+    return SV_OK;
+}
+
+// ---------------------------------------------------------------- autotuner
+// SV_MODE_AUTO measures instead of predicting: every candidate strategy is
+// planned (and compiled), run once to warm up and then timed with CUDA events
+// on a scratch state of the handle's size and dtype (cudaMalloc'ed for the
+// tuning and freed after it; its amplitudes do not change the time of these
+// kernels), and the fastest is kept.  The choice is remembered per device,
+// dtype, qubit count and circuit text, in the process and in the file
+// autotune.txt of the compiled-pass cache folder, so a later plan of the same
+// circuit (also in a later process) skips the timing.  Without room for a
+// scratch state the planner's own choice (tiled, else fused) is taken.
+
+std::vector<Strategy> candidates(const sv_state *h) {
+    std::vector<Strategy> v;
+    const int tile_m = h->dt == SV_C64 ? kTileM64 : kTileM128;
+    if (h->dt == SV_ENC2B) {
+        v.push_back(Strategy{SV_MODE_PERGATE, TileConfig{}, 0});
+        return v;
+    }
+    if (h->n >= tile_m) {
+        if (h->dt == SV_C64) {
+            // the generator's register bits, CTAs per SM and HBM I/O forms
+            const int opts[][3] = {{5, 2, 1}, {5, 2, 0}, {4, 2, 1}, {5, 3, 1}};
+            for (const auto &o : opts) v.push_back(Strategy{SV_MODE_TILED, tile_config64(o[0], o[1], o[2]), 0});
+        } else {
+            v.push_back(Strategy{SV_MODE_TILED, tile_config128(), 0});
+        }
+    } else {
+        v.push_back(Strategy{SV_MODE_PERGATE, TileConfig{}, 0});
+    }
+    for (int k = 3; k <= kMaxFusedQubits && k <= h->n; ++k) v.push_back(Strategy{SV_MODE_FUSED, TileConfig{}, k});
+    return v;
+}
+
+std::mutex g_tune_mu;
+std::unordered_map<std::string, std::string> g_tune;  // key -> chosen strategy name
+
+uint64_t fnv1a(const std::string &t) {
+    uint64_t x = 1469598103934665603ull;
+    for (unsigned char ch : t) x = (x ^ ch) * 1099511628211ull;
+    return x;
+}
+
+std::string tune_key(const sv_state *h, const char *text) {
+    cudaDeviceProp prop{};
+    cudaGetDeviceProperties(&prop, h->device);
+    char b[96];
+    std::snprintf(b, sizeof b, "%d|%d|%016llx", h->n, int(h->dt), static_cast<unsigned long long>(fnv1a(text)));
+    std::string name = prop.name;
+    for (char &ch : name)
+        if (ch == '\t' || ch == '\n') ch = ' ';
+    return name + "|" + b + "|" + tile_codegen_key();
+}
+
+std::string tune_file() {
+    const std::string dir = jit_cache_dir();
+    return dir.empty() ? std::string() : dir + "/autotune.txt";
+}
+
+// A remembered choice for key ("" if none): the process map, else the file.
+std::string tune_lookup(const std::string &key) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) return it->second;
+    const std::string path = tune_file();
+    if (path.empty()) return std::string();
+    std::string found;
+    if (FILE *f = std::fopen(path.c_str(), "r")) {
+        char line[1024];
+        while (std::fgets(line, sizeof line, f)) {
+            std::string ln(line);
+            while (!ln.empty() && (ln.back() == '\n' || ln.back() == '\r')) ln.pop_back();
+            const size_t tab = ln.find('\t');
+            if (tab != std::string::npos && ln.compare(0, tab, key) == 0) found = ln.substr(tab + 1);
+        }
+        std::fclose(f);
+    }
+    if (!found.empty()) g_tune[key] = found;
+    return found;
+}
+
+void tune_store(const std::string &key, const std::string &choice) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune[key] = choice;
+    const std::string path = tune_file();
+    if (path.empty()) return;
+    if (FILE *f = std::fopen(path.c_str(), "a")) {
+        std::fprintf(f, "%s\t%s\n", key.c_str(), choice.c_str());
+        std::fclose(f);
+    }
+}
+
+sv_status execute_direct(sv_plan_s *p);
+
+// Time each candidate on a scratch state; returns the index of the fastest
+// and a JSON report of all of them in *report.
+sv_status time_candidates(sv_state *h, const char *text, const Circuit &c, const std::vector<Strategy> &cand,
+                          size_t *best, std::string *report) {
+    size_t free_b = 0, total_b = 0;
+    SV_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+    if (h->bytes + (size_t(1) << 30) > free_b) {
+        *report = "{\"timed\": false, \"reason\": \"no device memory for a scratch state\"}";
+        return SV_ERR_OOM;
+    }
+    sv_state scratch;
+    scratch.n = h->n;
+    scratch.dt = h->dt;
+    scratch.bytes = h->bytes;
+    scratch.stream = h->stream;
+    scratch.device = h->device;
+    SV_CUDA_TRY(cudaMalloc(&scratch.data, h->bytes));
+    if (h->dt == SV_ENC2B) scratch.scales = reinterpret_cast<float *>(static_cast<char *>(scratch.data) + (size_t(2) << h->n));
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    sv_status s = SV_OK;
+    for (int i = 0; i < 2 && s == SV_OK; ++i)
+        if (cudaEventCreate(&ev[i]) != cudaSuccess) s = SV_ERR_CUDA;
+    std::string js = "{\"timed\": true, \"candidates\": [";
+    double best_ms = -1.0;
+    for (size_t i = 0; i < cand.size() && s == SV_OK; ++i) {
+        sv_plan_s *p = nullptr;
+        sv_status cs = create_plan(&scratch, text, c, cand[i], &p);
+        double ms = -1.0;
+        if (cs == SV_OK) {
+            cs = check_launch(launch_set_basis(&scratch, 0), "autotune");
+            if (!cs) cs = execute_direct(p);  // warm-up (module loads, one-time set-up)
+            const int reps = 2;
+            if (!cs && cudaEventRecord(ev[0], scratch.stream) != cudaSuccess) cs = SV_ERR_CUDA;
+            for (int r = 0; r < reps && !cs; ++r) cs = execute_direct(p);
+            if (!cs && cudaEventRecord(ev[1], scratch.stream) != cudaSuccess) cs = SV_ERR_CUDA;
+            if (!cs) cs = sync_stream(scratch.stream, "autotune");
+            float t = 0.0f;
+            if (!cs && cudaEventElapsedTime(&t, ev[0], ev[1]) == cudaSuccess) ms = double(t) / reps;
+            destroy_plan(p);
+        }
+        if (cs == SV_ERR_CUDA || cs == SV_ERR_TIMEOUT) s = cs;  // a device fault ends the tuning
+        char b[256];
+        std::snprintf(b, sizeof b, "%s{\"strategy\": \"%s\", \"ms\": %.4f%s}", i ? ", " : "",
+                      cand[i].name().c_str(), ms, cs ? ", \"failed\": true" : "");
+        js += b;
+        if (ms > 0 && (best_ms < 0 || ms < best_ms)) {
+            best_ms = ms;
+            *best = i;
+        }
+    }
+    for (cudaEvent_t e : ev)
+        if (e) cudaEventDestroy(e);
+    cudaStreamSynchronize(scratch.stream);
+    for (void *d : {static_cast<void *>(scratch.data), static_cast<void *>(scratch.d_partials),
+                    static_cast<void *>(scratch.d_idx), static_cast<void *>(scratch.d_amps), scratch.d_mat,
+                    static_cast<void *>(scratch.d_err), static_cast<void *>(scratch.d_expect)})
+        if (d) cudaFree(d);
+    scratch.data = nullptr;
+    js += "]";
+    if (best_ms > 0) js += ", \"chosen\": \"" + cand[*best].name() + "\"";
+    *report = js + "}";
+    if (s == SV_OK && best_ms < 0) {
+        set_error("autotune: no candidate ran");
+        s = SV_ERR_UNSUPPORTED;
+    }
+    return s;
+}
+
+sv_status create_auto_plan(sv_state *h, const char *text, const Circuit &c, sv_plan_s **out) {
+    const std::vector<Strategy> cand = candidates(h);
+    const std::string key = tune_key(h, text);
+    const std::string known = tune_lookup(key);
+    for (const Strategy &st : cand)
+        if (!known.empty() && st.name() == known) {
+            sv_status s = create_plan(h, text, c, st, out);
+            if (!s) (*out)->tuning = "{\"timed\": false, \"remembered\": true, \"chosen\": \"" + known + "\"}";
+            return s;
+        }
+    size_t best = 0;
+    std::string report;
+    sv_status s = time_candidates(h, text, c, cand, &best, &report);
+    if (s == SV_ERR_OOM) {
+        // no room to time: the planner's own choice
+        Strategy st{h->dt == SV_ENC2B ? SV_MODE_PERGATE : SV_MODE_TILED, default_config(h), 0};
+        s = create_plan(h, text, c, st, out);
+        if (!s) (*out)->tuning = report;
+        return s;
+    }
+    if (s) return s;
+    tune_store(key, cand[best].name());
+    s = create_plan(h, text, c, cand[best], out);
+    if (!s) (*out)->tuning = report;
+    return s;
 }
 
 }  // namespace
@@ -165,71 +441,42 @@ sv_status sv_plan_create(sv_handle h, const char *text, int mode, sv_plan *out) 
         set_error("NULL handle");
         return SV_ERR_ARG;
     }
-    if (mode != SV_MODE_PERGATE && mode != SV_MODE_TILED && mode != SV_MODE_FUSED) {
+    if (mode != SV_MODE_PERGATE && mode != SV_MODE_TILED && mode != SV_MODE_FUSED && mode != SV_MODE_AUTO) {
         set_error("unknown mode %d", mode);
         return SV_ERR_ARG;
     }
-    if (h->dt == SV_ENC2B && mode != SV_MODE_PERGATE) {
+    if (h->dt == SV_ENC2B && mode != SV_MODE_PERGATE && mode != SV_MODE_AUTO) {
         set_error("the two-byte code runs one decode-gate-encode pass per gate (SV_MODE_PERGATE)");
         return SV_ERR_DTYPE;
     }
-    const int tile_m = h->dt == SV_C64 ? kTileM64 : kTileM128;
-    const bool tiled = mode == SV_MODE_TILED && h->n >= tile_m;
-    std::string key;
-    if (tiled && text) {
-        key = tile_cache_key(h, text);
-        std::lock_guard<std::mutex> lock(g_tile_cache_mu);
-        auto it = g_tile_cache.find(key);
-        if (it != g_tile_cache.end()) {
-            sv_plan_s *p = new sv_plan_s;
-            p->h = h;
-            p->mode = mode;
-            p->gates = it->second.gates;
-            p->tfns = it->second.fns;
-            p->tile_rb = it->second.rb;
-            const double pass_bytes = 2.0 * double(uint64_t(1) << h->n) * (h->dt == SV_C64 ? 8.0 : 16.0);
-            for (size_t i = 0; i < p->tfns.size(); ++i) {
-                p->launches.push_back(PlanLaunch{1, int(i), pass_bytes});
-                p->bytes += pass_bytes;
-            }
-            h->live_plans++;
-            *out = p;
-            return SV_OK;
-        }
+    if (!text) {
+        set_error("NULL circuit text");
+        return SV_ERR_ARG;
     }
     Circuit c;
-    sv_status s = parse_circuit(text, h->n, &c);
-    if (s) return s;
-    sv_plan_s *p = new sv_plan_s;
-    p->h = h;
-    p->mode = mode;
-    p->gates = int64_t(c.instrs.size());
-    if (mode == SV_MODE_FUSED) {
-        s = build_fused_plan(h, c, p);
-        if (s) {
-            destroy_plan(p);
-            return s;
-        }
-    } else if (mode == SV_MODE_PERGATE || h->n < tile_m) {
-        // per-gate updates (also the tiled mode's path for states smaller than one tile)
-        p->pergate = lower_to_gate1(c);
-        for (size_t i = 0; i < p->pergate.size(); ++i) {
-            const double b = gate1_bytes(h, p->pergate[i]);
-            p->launches.push_back(PlanLaunch{0, int(i), b});
-            p->bytes += b;
-        }
-    } else {
-        s = build_tile_plan(h, c, p);
-        if (s) {
-            destroy_plan(p);
-            return s;
-        }
-        if (!key.empty()) {
-            std::lock_guard<std::mutex> lock(g_tile_cache_mu);
-            if (g_tile_cache.size() >= kTileCacheMax) g_tile_cache.clear();
-            g_tile_cache[key] = TileCacheEntry{p->tfns, p->tile_rb, p->gates};
-        }
+    sv_status s = SV_OK;
+    // a cached tiled plan needs no parse (the text is part of its key)
+    const Strategy st{mode, default_config(h), 0};
+    const bool maybe_cached = mode == SV_MODE_TILED;
+    if (!maybe_cached) {
+        s = parse_circuit(text, h->n, &c);
+        if (s) return s;
     }
+    sv_plan_s *p = nullptr;
+    if (mode == SV_MODE_AUTO) {
+        s = create_auto_plan(h, text, c, &p);
+    } else {
+        if (maybe_cached) {
+            std::lock_guard<std::mutex> lock(g_tile_cache_mu);
+            if (!g_tile_cache.count(tile_cache_key(h, st.cfg, text))) s = SV_ERR_PARSE;  // not cached: parse below
+        }
+        if (s == SV_ERR_PARSE) {
+            s = parse_circuit(text, h->n, &c);
+            if (s) return s;
+        }
+        s = create_plan(h, text, c, st, &p);
+    }
+    if (s) return s;
     h->live_plans++;
     *out = p;
     return SV_OK;
@@ -245,6 +492,26 @@ sv_status execute_direct(sv_plan_s *p) {
     }
     return SV_OK;
 }
+
+}  // namespace
+
+extern "C++" {
+cudaError_t plan_launch_all(sv_plan_s *p) {
+    for (const PlanLaunch &l : p->launches) {
+        const cudaError_t e = launch_one(p, l);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+bool plan_capturable(const sv_plan_s *p) {
+    for (const PlanLaunch &l : p->launches)
+        if (l.kind == 3) return false;  // host matrix copies per launch
+    return true;
+}
+}  // extern "C++"
+
+namespace {
 
 // Graph replay applies to plans of two or more launches that are kernel
 // launches only (the CUDA-core dense blocks copy their matrix from host
@@ -394,7 +661,7 @@ sv_status sv_plan_stats(const char *text, int n, sv_dtype dt, int compile, int64
             return SV_ERR_UNSUPPORTED;
         }
         TilePlan<float> tp;
-        s = plan_tiles<float>(c, n, TileConfig{kTileM64, tile_rb64(), tile_low64(), true}, &tp);
+        s = plan_tiles<float>(c, n, tile_config64(), &tp);
         return s ? s : count(tp);
     }
     if (n < kTileM128) {
@@ -402,8 +669,74 @@ sv_status sv_plan_stats(const char *text, int n, sv_dtype dt, int compile, int64
         return SV_ERR_UNSUPPORTED;
     }
     TilePlan<double> tp;
-    s = plan_tiles<double>(c, n, TileConfig{kTileM128, kTileRB128, kTileLow128, false}, &tp);
+    s = plan_tiles<double>(c, n, tile_config128(), &tp);
     return s ? s : count(tp);
+}
+
+sv_status sv_plan_launch_stats(sv_plan p, int64_t i, double *fp32_ops_per_amplitude, int64_t *segments) {
+    if (!p || i < 0 || i >= int64_t(p->launches.size())) {
+        set_error("bad plan or launch index");
+        return SV_ERR_ARG;
+    }
+    const PlanLaunch &l = p->launches[size_t(i)];
+    if (fp32_ops_per_amplitude) *fp32_ops_per_amplitude = l.lane_ops;
+    if (segments) *segments = l.segments;
+    return SV_OK;
+}
+
+sv_status sv_plan_pass_source(const char *text, int n, sv_dtype dt, int64_t pass, char *buf, size_t cap,
+                              size_t *len) {
+    if (!text || n < 1 || n > kMaxQubits || (dt != SV_C64 && dt != SV_C128) || pass < 0) {
+        set_error("bad arguments");
+        return SV_ERR_ARG;
+    }
+    Circuit c;
+    sv_status s = parse_circuit(text, n, &c);
+    if (s) return s;
+    auto emit = [&](auto &tp) -> sv_status {
+        if (pass >= int64_t(tp.passes.size())) {
+            set_error("pass %lld of a %zu-pass plan", (long long)pass, tp.passes.size());
+            return SV_ERR_ARG;
+        }
+        const std::string src = tile_pass_source(tp, size_t(pass));
+        if (len) *len = src.size();
+        if (buf && cap > 0) {
+            const size_t k = src.size() < cap - 1 ? src.size() : cap - 1;
+            std::memcpy(buf, src.data(), k);
+            buf[k] = '\0';
+        }
+        return SV_OK;
+    };
+    if (dt == SV_C64) {
+        if (n < kTileM64) {
+            set_error("tiled passes need n >= %d", kTileM64);
+            return SV_ERR_UNSUPPORTED;
+        }
+        TilePlan<float> tp;
+        s = plan_tiles<float>(c, n, tile_config64(), &tp);
+        return s ? s : emit(tp);
+    }
+    if (n < kTileM128) {
+        set_error("tiled passes need n >= %d", kTileM128);
+        return SV_ERR_UNSUPPORTED;
+    }
+    TilePlan<double> tp;
+    s = plan_tiles<double>(c, n, tile_config128(), &tp);
+    return s ? s : emit(tp);
+}
+
+sv_status sv_plan_tuning(sv_plan p, char *buf, size_t cap, size_t *len) {
+    if (!p) {
+        set_error("NULL plan");
+        return SV_ERR_ARG;
+    }
+    if (len) *len = p->tuning.size();
+    if (buf && cap > 0) {
+        const size_t k = p->tuning.size() < cap - 1 ? p->tuning.size() : cap - 1;
+        std::memcpy(buf, p->tuning.data(), k);
+        buf[k] = '\0';
+    }
+    return SV_OK;
 }
 
 sv_status sv_plan_free(sv_plan p) {

@@ -1,6 +1,7 @@
 // Circuit plans: the host-side planner output that sv_plan_execute replays.
 #pragma once
 
+#include <string>
 #include <vector>
 
 #include "fused_tc.h"
@@ -47,6 +48,8 @@ struct PlanLaunch {
                    // 2: tensor-core block tcargs[index]; 3: CUDA-core block blocks[index]
     int index;
     double bytes;  // algorithmic bytes
+    double lane_ops = 0.0;  // compiled tile passes: FP32 lane operations per amplitude (at least)
+    int segments = 0;       // compiled tile passes: register segments
 };
 
 struct sv_plan_s {
@@ -56,6 +59,9 @@ struct sv_plan_s {
     std::vector<sv::Gate1> pergate;        // per-gate updates
     std::vector<void *> tfns;              // compiled tile passes
     int tile_rb = 0;                       // their register bits per thread
+    std::vector<double> tile_lane_ops;     // their FP32 lane operations per amplitude
+    std::vector<int> tile_nseg;            // their register segments
+    std::string tuning;                    // SV_MODE_AUTO: the measured candidates (JSON), else empty
     std::vector<sv::FusedBlock> blocks;    // fused blocks (CUDA-core kernel)
     std::vector<sv::TcArgs> tcargs;        // fused blocks (tensor-core kernel)
     void *d_tcA = nullptr;                 // their operand images, kTcOperandBytes each
@@ -73,3 +79,11 @@ struct sv_plan_s {
     cudaEvent_t gev[2] = {nullptr, nullptr};
     cudaGraphExec_t gexec = nullptr;
 };
+
+namespace sv {
+// Every launch of a plan, in order, on the stream of its handle (no graph).
+cudaError_t plan_launch_all(sv_plan_s *p);
+// Whether a plan's launches can be captured into a CUDA graph (no host-side
+// copies between them).
+bool plan_capturable(const sv_plan_s *p);
+}  // namespace sv

@@ -47,6 +47,14 @@ enum StructKind : int32_t {
     SK_COUNT = 6
 };
 
+// Planner gate conditions on bits kParamBit0 + j (above every state qubit)
+// test bit j of a launch parameter instead of an amplitude index bit: one
+// compiled pass then serves every value of those bits (the fixed branch bits
+// of a decomposition's branch parts).
+constexpr int kParamBit0 = 48;
+constexpr int kParamBits = 16;
+constexpr uint64_t kQubitBits = (uint64_t(1) << kParamBit0) - 1;
+
 template <typename R>
 struct alignas(16) TileOp {
     int32_t type;
@@ -54,6 +62,7 @@ struct alignas(16) TileOp {
     uint32_t rmask, rval;  // condition on the register index (TOP_G1 controls)
     uint32_t tmask, tval;  // condition on the thread's tile-index bits
     uint64_t gmask, gval;  // condition on the CTA's outer global index bits
+    uint32_t pmask, pval;  // condition on the launch parameter bits
     R u[8];
 };
 
@@ -83,14 +92,24 @@ struct TileConfig {
     int rb;     // register bits per thread
     int low;    // low qubits always in the tile (contiguous runs of 2^low amplitudes)
     bool c64;
+    int ctas = 2;        // CTAs per SM the passes are compiled for (register budget)
+    bool direct = true;  // complex64: first / last segment straight between HBM and registers
 };
 
 template <typename R>
 struct TilePlan {
     int m = 0, rb = 0;  // tile bits, register bits per thread
+    int ctas = 2;
+    bool direct = true;
     std::vector<TilePassArgs> passes;
     std::vector<TileOp<R>> ops;
     std::vector<TileSeg> segs;
+    // per pass: FP32 lane operations per amplitude its gates need at least
+    // (2 per structured butterfly, 1 per T-type phase, 4 per other complex
+    // phase or 8 per dense 2x2, times the fraction of amplitudes a control
+    // or condition leaves; sign flips and X are free), and its segments
+    std::vector<double> lane_ops;
+    std::vector<int> nseg;
 };
 
 // A gate in the planner's form.  kind 0: 2x2 update u on `target` where
@@ -122,6 +141,9 @@ sv_status plan_tiles(const Circuit &circ, int n, const TileConfig &cfg, TilePlan
 constexpr int kTileM64 = 13, kTileRB64 = 5, kTileLow64 = 4;
 constexpr int kTileM128 = 12, kTileRB128 = 4, kTileLow128 = 3;
 
+// The generated CUDA source of pass i of a plan (what jit_tile_plan compiles).
+std::string tile_pass_source(const TilePlan<float> &tp, size_t i);
+std::string tile_pass_source(const TilePlan<double> &tp, size_t i);
 // Compile every pass of a plan into a straight-line kernel (NVRTC, cached
 // per device and source); fns receives one CUfunction per pass.
 sv_status jit_tile_plan(const TilePlan<float> &tp, std::vector<void *> *fns);
@@ -132,12 +154,23 @@ sv_status jit_compile_check(const TilePlan<double> &tp);
 // Register bits per thread of complex64 tile passes (SV_TILE_RB overrides,
 // 4 or 5).
 int tile_rb64();
+// CTAs per SM of the pass kernels (SV_TILE_CTAS overrides, 1 to 3).
+int tile_ctas_per_sm();
+// The tile configuration of complex64 / complex128 passes: the environment's
+// defaults, or the given register bits, CTAs per SM and direct I/O (an
+// autotuner's candidate; 0 / -1 keep the default).
+TileConfig tile_config64(int rb = 0, int ctas = 0, int direct = -1);
+TileConfig tile_config128();
+// Folder of the compiled-pass disk cache ("" when there is none).
+std::string jit_cache_dir();
+// A short text naming a configuration (plan keys, tuning reports).
+std::string tile_config_name(const TileConfig &cfg);
 // Low qubits always in a complex64 tile (contiguous HBM runs of 2^low
 // amplitudes); SV_TILE_LOW overrides (4 to 10).
 int tile_low64();
 // Launch one compiled pass over the whole state (grid = 2^(n-m) CTAs of
-// 2^(m-rb) threads).
-cudaError_t launch_jit_pass(sv_state *h, void *fn, int n, int rb);
+// 2^(m-rb) threads); param: the launch parameter bits (kParamBit0).
+cudaError_t launch_jit_pass(sv_state *h, void *fn, int n, int rb, uint64_t param = 0);
 const char *tile_kernel_name(const sv_state *h);
 // The code-generation switches (environment) that shape a compiled pass, as
 // part of a plan-cache key.

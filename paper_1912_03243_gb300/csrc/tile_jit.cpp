@@ -109,13 +109,6 @@ bool packed_adds_enabled() {
 }
 
 
-// CTAs per SM the pass kernels are compiled for (register budget); the
-// shared tile (64 KiB) allows up to 3.  SV_TILE_CTAS overrides.
-int tile_ctas_per_sm() {
-    const char *e = std::getenv("SV_TILE_CTAS");
-    const int v = e ? std::atoi(e) : 2;
-    return v >= 1 && v <= 3 ? v : 2;
-}
 
 // Which ends of a pass go straight between HBM and registers: direct I/O on,
 // complex64, and lanes of the first (last) segment that cover at least the 3
@@ -136,7 +129,7 @@ HbmIo hbm_io(const TilePlan<R> &tp, size_t pass) {
             last = tp.ops[size_t(i)].a;
             ++nseg;
         }
-    const bool on = sizeof(R) == 4 && direct_io_enabled() && first >= 0;
+    const bool on = sizeof(R) == 4 && tp.direct && first >= 0;
     auto contiguous = [&](int sidx) {
         const TileSeg &sg = tp.segs[size_t(sidx)];
         uint32_t lanes = 0;
@@ -191,8 +184,8 @@ std::string gen_pass(const TilePlan<R> &tp, size_t pass) {
     };
     int tpos[kTileMaxQ];
     for (int k = 0; k < tbits; ++k) tpos[k] = pa.tile_pos[k + G.EPC_LOG];
-    o << "extern \"C\" __global__ void __launch_bounds__(" << G.NT << ", " << tile_ctas_per_sm() << ") svp(" << C2T
-      << "* __restrict__ psi) {\n";
+    o << "extern \"C\" __global__ void __launch_bounds__(" << G.NT << ", " << tp.ctas << ") svp(" << C2T
+      << "* __restrict__ psi, const u64 prm) {\n";
     o << "  extern __shared__ __align__(16) unsigned char smem[];\n";
     o << "  " << C2T << "* sm = reinterpret_cast<" << C2T << "*>(smem);\n";
     // the CTA index is the tile number; conditions on outer qubits test
@@ -386,11 +379,13 @@ std::string gen_pass(const TilePlan<R> &tp, size_t pass) {
         // runtime condition on thread / CTA bits (branch-free select)
         std::string cond;
         int cid = -1;
-        if (op.tmask || op.gmask) {
+        if (op.tmask || op.gmask || op.pmask) {
             cid = cond_id++;
             cond = "c" + std::to_string(cid);
             o << "  const bool " << cond << " = ((jt & " << op.tmask << "u) == " << op.tval << "u) && ((cta & "
-              << compress(op.gmask) << "ull) == " << compress(op.gval) << "ull);\n";
+              << compress(op.gmask) << "ull) == " << compress(op.gval) << "ull)";
+            if (op.pmask) o << " && ((prm & " << op.pmask << "ull) == " << op.pval << "ull)";
+            o << ";\n";
             if (op.type == TOP_NEG) o << "  const " << RT << " sg" << cid << " = " << cond << " ? " << RT << "(-1) : " << RT << "(1);\n";
         }
         auto sel = [&](const std::string &v_new, const std::string &v_old) {
@@ -975,11 +970,42 @@ bool direct_io_enabled() {
     return !(e && e[0] == '0');
 }
 
+// CTAs per SM the pass kernels are compiled for (register budget); the
+// shared tile (64 KiB) allows up to 3.  SV_TILE_CTAS overrides.
+int tile_ctas_per_sm() {
+    const char *e = std::getenv("SV_TILE_CTAS");
+    const int v = e ? std::atoi(e) : 2;
+    return v >= 1 && v <= 3 ? v : 2;
+}
+
+TileConfig tile_config64(int rb, int ctas, int direct) {
+    TileConfig c{kTileM64, rb ? rb : tile_rb64(), tile_low64(), true};
+    c.ctas = ctas ? ctas : tile_ctas_per_sm();
+    c.direct = direct < 0 ? direct_io_enabled() : direct != 0;
+    return c;
+}
+
+TileConfig tile_config128() {
+    TileConfig c{kTileM128, kTileRB128, kTileLow128, false};
+    c.ctas = tile_ctas_per_sm();
+    c.direct = false;
+    return c;
+}
+
+std::string tile_config_name(const TileConfig &cfg) {
+    return "m=" + std::to_string(cfg.m) + ",rb=" + std::to_string(cfg.rb) + ",low=" + std::to_string(cfg.low) +
+           ",ctas=" + std::to_string(cfg.ctas) + ",direct=" + std::to_string(int(cfg.direct));
+}
+
+std::string jit_cache_dir() { return cache_dir(); }
+
 std::string tile_codegen_key() {
     return "f32x2=" + std::to_string(int(packed_adds_enabled())) + ",ctas=" + std::to_string(tile_ctas_per_sm()) +
            ",direct=" + std::to_string(int(direct_io_enabled()));
 }
 
+std::string tile_pass_source(const TilePlan<float> &tp, size_t i) { return gen_pass(tp, i); }
+std::string tile_pass_source(const TilePlan<double> &tp, size_t i) { return gen_pass(tp, i); }
 sv_status jit_tile_plan(const TilePlan<float> &tp, std::vector<void *> *fns) { return jit_plan_impl(tp, fns); }
 sv_status jit_tile_plan(const TilePlan<double> &tp, std::vector<void *> *fns) { return jit_plan_impl(tp, fns); }
 sv_status jit_compile_check(const TilePlan<float> &tp) { return compile_check_impl(tp); }
@@ -990,7 +1016,7 @@ const char *tile_kernel_name(const sv_state *h) {
     return h->dt == SV_C64 ? n64[tile_rb64() - 4] : "svp<f64,12,4>";
 }
 
-cudaError_t launch_jit_pass(sv_state *h, void *fn, int n, int rb) {
+cudaError_t launch_jit_pass(sv_state *h, void *fn, int n, int rb, uint64_t param) {
     const int M = h->dt == SV_C64 ? kTileM64 : kTileM128;
     size_t tile_bytes = (size_t(1) << M) * (h->dt == SV_C64 ? 8u : 16u);
     {
@@ -999,7 +1025,8 @@ cudaError_t launch_jit_pass(sv_state *h, void *fn, int n, int rb) {
         if (it != g_jit_smem.end()) tile_bytes = size_t(it->second);
     }
     void *psi = h->data;
-    void *args[] = {&psi};
+    unsigned long long prm = param;
+    void *args[] = {&psi, &prm};
     return cudaLaunchKernel(static_cast<const void *>(fn), dim3(1u << (n - M)), dim3(1u << (M - rb)), args, tile_bytes,
                             h->stream);
 }

@@ -463,8 +463,12 @@ sv_status plan_tiles_one(const std::vector<PGate> &G, int n, const TileConfig &c
     out->passes.clear();
     out->ops.clear();
     out->segs.clear();
+    out->lane_ops.clear();
+    out->nseg.clear();
     out->m = cfg.m;
     out->rb = cfg.rb;
+    out->ctas = cfg.ctas;
+    out->direct = cfg.c64 && cfg.direct;
     const int m = cfg.m, rb = cfg.rb, L = cfg.low;
     if (n < m) {
         set_error("tiled mode needs n >= %d", m);
@@ -529,6 +533,25 @@ sv_status plan_tiles_one(const std::vector<PGate> &G, int n, const TileConfig &c
         }
         pa.op_begin = int(out->ops.size());
 
+        // ---- the FP32 work the pass's gates need at least, per amplitude
+        {
+            double ops = 0.0;
+            for (int idx : pass_ops) {
+                const PGate &g = G[size_t(idx)];
+                const double frac = std::ldexp(1.0, -popc(g.cmask & kQubitBits));
+                if (g.kind == 0) {
+                    cd c;
+                    const int kind = struct_kind(g.u, &c);
+                    ops += frac * (kind == SK_X ? 0.0 : kind >= 0 ? 2.0 : 8.0);
+                } else if (toc(g.scale) == cd(1)) {
+                    const cd ph = toc(g.u[0]);
+                    const double ar = std::fabs(ph.real()), ai = std::fabs(ph.imag());
+                    if (ph == cd(1) || ph == cd(-1) || ph == cd(0)) continue;
+                    ops += frac * (std::fabs(ar - ai) <= 4e-7 * ar ? 2.0 : 4.0);
+                }
+            }
+            out->lane_ops.push_back(ops);
+        }
         // ---- segments (list scheduling over register slots)
         std::vector<int> remaining = pass_ops;
         cd scale = 1;
@@ -618,10 +641,16 @@ sv_status plan_tiles_one(const std::vector<PGate> &G, int n, const TileConfig &c
             for (int idx : seg_ops) {
                 const PGate &g = G[size_t(idx)];
                 TileOp<R> op{};
-                for (int q = 0; q < n; ++q) {
+                for (int q = 0; q < 64; ++q) {
                     if (!(g.cmask >> q & 1)) continue;
                     const uint64_t want = g.cval >> q & 1;
-                    if (tpos_of[q] < 0) {
+                    if (q >= kParamBit0) {
+                        op.pmask |= 1u << (q - kParamBit0);
+                        op.pval |= uint32_t(want) << (q - kParamBit0);
+                    } else if (q >= n) {
+                        set_error("gate condition on qubit %d of a %d-qubit state", q, n);
+                        return SV_ERR_ARG;
+                    } else if (tpos_of[q] < 0) {
                         op.gmask |= uint64_t(1) << q;
                         op.gval |= want << q;
                     } else if (slot_of_tbit[tpos_of[q]] >= 0) {
@@ -668,7 +697,12 @@ sv_status plan_tiles_one(const std::vector<PGate> &G, int n, const TileConfig &c
         }
         flush_scale();
         pa.op_end = int(out->ops.size());
-        if (cfg.c64 && direct_io_enabled()) {
+        {
+            int ns = 0;
+            for (int i = pa.op_begin; i < pa.op_end; ++i) ns += out->ops[size_t(i)].type == TOP_SEG;
+            out->nseg.push_back(ns);
+        }
+        if (cfg.c64 && cfg.direct) {
             // the first and last segments load from and store to HBM straight
             // from registers when tile bits 0-2 are free for lanes: their lanes
             // then take the lowest free tile bits (contiguous amplitudes), so a

@@ -3,9 +3,10 @@ term of the Eq. 3 sum is independent; the paper distributes them over MPI
 ranks).
 
 The 2^S branches are split into 2^p parts by their low p bits
-(p = ceil(log2(world))); rank r sums parts r, r + world, ... and one FP64
-all-reduce of the m complex amplitudes combines them.  That all-reduce is
-the only collective of the path.
+(p = ceil(log2(world))); rank r takes the parts r, r + world, ...  The
+library sums a rank's parts on its GPU in FP64 (sv_cut_amplitudes_parts);
+this module only assigns the parts and runs the one collective of the path,
+an FP64 all-reduce of the m complex amplitudes.
 """
 
 from __future__ import annotations
@@ -23,20 +24,21 @@ def parts_for_rank(rank: int, world: int) -> tuple[int, list[int]]:
     return p, [part for part in range(1 << p) if part % world == rank]
 
 
-def sharded_sum(partial_fn, m: int, group=None) -> np.ndarray:
-    """Sum partial_fn(part, nparts_log2) -> complex128[m] over this rank's
-    parts, then all-reduce (FP64) across the process group; every rank
-    returns the full sum."""
+def sharded_sum(rank_sum_fn, m: int, group=None) -> np.ndarray:
+    """rank_sum_fn(nparts_log2, parts) -> complex128[m] is this rank's share
+    of the sum (the library's sv_cut_amplitudes_parts, or a CPU stand-in in
+    tests); the shares are all-reduced (FP64) across the process group and
+    every rank returns the full sum."""
     import torch
     import torch.distributed as dist
 
     world = dist.get_world_size(group)
     rank = dist.get_rank(group)
     p, parts = parts_for_rank(rank, world)
-    acc = np.zeros(m, dtype=np.complex128)
-    for part in parts:
-        acc += np.asarray(partial_fn(part, p), dtype=np.complex128)
-    buf = torch.from_numpy(acc.view(np.float64).copy())
+    share = np.ascontiguousarray(rank_sum_fn(p, parts), dtype=np.complex128)
+    if share.shape != (m,):
+        raise ValueError(f"rank {rank}: share of shape {share.shape}, expected ({m},)")
+    buf = torch.from_numpy(share.view(np.float64).copy())
     if dist.get_backend(group) == "nccl":
         buf = buf.cuda()
     dist.all_reduce(buf, op=dist.ReduceOp.SUM, group=group)
@@ -49,8 +51,8 @@ def cut_amplitudes_sharded(circuit, n: int, mask_a: int, z, form: int = 0, group
     from paper_1912_03243_gb300 import sv
 
     zz = np.ascontiguousarray(z, dtype=np.uint64)
-    return sharded_sum(lambda part, p: sv.sv_cut_amplitudes_part(circuit, n, mask_a, zz, part, p, form)[0], zz.size,
-                       group)
+    return sharded_sum(lambda p, parts: sv.sv_cut_amplitudes_parts(circuit, n, mask_a, zz, p, parts, form)[0],
+                       zz.size, group)
 
 
 def cut_amplitudes_multi_sharded(circuit, n: int, part_of, z_words, form: int = 0, group=None) -> np.ndarray:
@@ -60,5 +62,5 @@ def cut_amplitudes_multi_sharded(circuit, n: int, part_of, z_words, form: int = 
 
     zz = np.ascontiguousarray(z_words, dtype=np.uint64).reshape(-1, (n + 63) // 64)
     return sharded_sum(
-        lambda part, p: sv.sv_cut_amplitudes_multi(circuit, n, part_of, zz, form, part=part, nparts_log2=p)[0],
+        lambda p, parts: sv.sv_cut_amplitudes_multi_parts(circuit, n, part_of, zz, p, parts, form)[0],
         zz.shape[0], group)

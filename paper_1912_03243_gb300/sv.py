@@ -20,8 +20,8 @@ LIB_PATH = os.path.join(_HERE, "libsv.so")
 
 SV_C64, SV_C128, SV_ENC2B = 0, 1, 2
 DTYPES = {"c64": SV_C64, "c128": SV_C128, "enc2b": SV_ENC2B}
-SV_MODE_PERGATE, SV_MODE_TILED, SV_MODE_FUSED = 0, 1, 2
-MODES = {"pergate": SV_MODE_PERGATE, "tiled": SV_MODE_TILED, "fused": SV_MODE_FUSED}
+SV_MODE_PERGATE, SV_MODE_TILED, SV_MODE_FUSED, SV_MODE_AUTO = 0, 1, 2, 3
+MODES = {"pergate": SV_MODE_PERGATE, "tiled": SV_MODE_TILED, "fused": SV_MODE_FUSED, "auto": SV_MODE_AUTO}
 
 STATUS = {0: "SV_OK", 1: "SV_ERR_ARG", 2: "SV_ERR_OOM", 3: "SV_ERR_DTYPE", 4: "SV_ERR_CUDA",
           5: "SV_ERR_TIMEOUT", 6: "SV_ERR_STATE", 7: "SV_ERR_PARSE", 8: "SV_ERR_UNSUPPORTED"}
@@ -54,6 +54,10 @@ SIGNATURES = {
     "sv_plan_free": (_st, [_vp]),
     "sv_plan_stats": (_st, [ctypes.c_char_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, _i64p, _i64p, _i64p]),
     "sv_plan_launch_info": (_st, [_vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_char_p), _dp]),
+    "sv_plan_launch_stats": (_st, [_vp, ctypes.c_int64, _dp, _i64p]),
+    "sv_plan_tuning": (_st, [_vp, ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
+    "sv_plan_pass_source": (_st, [ctypes.c_char_p, ctypes.c_int, ctypes.c_int, ctypes.c_int64, ctypes.c_char_p,
+                                  ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
     "sv_encode2b": (_st, [_vp, _vp]),
     "sv_decode2b": (_st, [_vp, _vp]),
     "sv_get_codes": (_st, [_vp, ctypes.POINTER(ctypes.c_int8), ctypes.POINTER(ctypes.c_float)]),
@@ -70,6 +74,17 @@ SIGNATURES = {
     "sv_cut_amplitudes_multi": (_st, [ctypes.c_char_p, ctypes.c_int, ctypes.POINTER(ctypes.c_uint8), ctypes.c_int,
                                       ctypes.c_int, ctypes.c_uint64, ctypes.c_int, ctypes.c_size_t, _u64p, _dp,
                                       ctypes.POINTER(ctypes.c_int), _vp]),
+    "sv_cut_amplitudes_parts": (_st, [ctypes.c_char_p, ctypes.c_int, ctypes.c_uint64, ctypes.c_int, ctypes.c_int,
+                                      ctypes.c_size_t, _u64p, ctypes.c_size_t, _u64p, _dp, _ip, _vp]),
+    "sv_cut_amplitudes_multi_parts": (_st, [ctypes.c_char_p, ctypes.c_int, ctypes.POINTER(ctypes.c_uint8),
+                                            ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_size_t, _u64p,
+                                            ctypes.c_size_t, _u64p, _dp, _ip, _vp]),
+    "sv_batch_create": (_st, [ctypes.POINTER(_vp), ctypes.POINTER(ctypes.c_char_p), ctypes.c_int,
+                              ctypes.POINTER(_vp)]),
+    "sv_batch_execute": (_st, [_vp]),
+    "sv_batch_info": (_st, [_vp, _i64p, _i64p, _dp, ctypes.POINTER(ctypes.c_int)]),
+    "sv_batch_free": (_st, [_vp]),
+    "sv_run_batch": (_st, [ctypes.POINTER(_vp), ctypes.POINTER(ctypes.c_char_p), ctypes.c_int]),
     "sv_gate_matrix": (ctypes.c_int, [ctypes.c_char_p, _dp, ctypes.c_int, _dp]),
     "sv_version": (ctypes.c_char_p, []),
 }
@@ -143,6 +158,31 @@ def sv_cut_amplitudes(circuit, n: int, mask_a: int, z, form: int = 0, stream=Non
     return out.view(np.complex128).copy(), s.value
 
 
+def sv_plan_pass_source(circuit, n: int, dtype: str | int, pass_index: int) -> str:
+    """Host-only: the generated CUDA source of one pass of the tiled plan."""
+    ln = ctypes.c_size_t(0)
+    t, dt = _text(circuit), DTYPES.get(dtype, dtype)
+    _check(lib().sv_plan_pass_source(t, n, dt, pass_index, None, 0, ctypes.byref(ln)), "sv_plan_pass_source")
+    buf = ctypes.create_string_buffer(ln.value + 1)
+    _check(lib().sv_plan_pass_source(t, n, dt, pass_index, buf, ln.value + 1, ctypes.byref(ln)),
+           "sv_plan_pass_source")
+    return buf.value.decode()
+
+
+def tiled_pass_sources(case: str) -> str:
+    """Generated sources of every pass of a named tiled case, concatenated:
+    "random <n> <depth> <seed> <dtype>" (the random circuit family)."""
+    from paper_1912_03243_gb300 import circuits as C
+
+    kind, n, depth, seed, dtype = case.split()
+    if kind != "random":
+        raise ValueError(f"unknown case {case!r}")
+    n, depth, seed = int(n), int(depth), int(seed)
+    circ = C.random_circuit(n, depth, seed)
+    _, passes, _ = sv_plan_stats(circ, n, dtype)
+    return "".join(sv_plan_pass_source(circ, n, dtype, i) for i in range(passes))
+
+
 def sv_plan_stats(circuit, n: int, dtype: str | int = "c64", compile: bool = False):
     """Host-only tiled planning statistics: (gates, passes, segments)."""
     g, p, s = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
@@ -178,6 +218,41 @@ def sv_cut_amplitudes_part(circuit, n: int, mask_a: int, z, part: int, nparts_lo
     _check(lib().sv_cut_amplitudes_part(_text(circuit), n, ctypes.c_uint64(mask_a), form, ctypes.c_uint64(part),
                                         nparts_log2, zz.size, zz.ctypes.data_as(_u64p), _dptr(out), ctypes.byref(s),
                                         _vp(st)), "sv_cut_amplitudes_part")
+    return out.view(np.complex128).copy(), s.value
+
+
+def sv_cut_amplitudes_parts(circuit, n: int, mask_a: int, z, nparts_log2: int, parts, form: int = 0,
+                            stream=None):
+    """Eq. 3 summed over the listed branch parts (each < 2^nparts_log2), in
+    FP64 on the device: (amplitudes, S)."""
+    import torch
+
+    zz = np.ascontiguousarray(z, dtype=np.uint64)
+    pl = np.ascontiguousarray(parts, dtype=np.uint64)
+    out = np.zeros(2 * zz.size, dtype=np.float64)
+    s = ctypes.c_int(0)
+    st = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+    _check(lib().sv_cut_amplitudes_parts(_text(circuit), n, ctypes.c_uint64(mask_a), form, nparts_log2, pl.size,
+                                         pl.ctypes.data_as(_u64p), zz.size, zz.ctypes.data_as(_u64p), _dptr(out),
+                                         ctypes.byref(s), _vp(st)), "sv_cut_amplitudes_parts")
+    return out.view(np.complex128).copy(), s.value
+
+
+def sv_cut_amplitudes_multi_parts(circuit, n: int, part_of, z_words, nparts_log2: int, parts, form: int = 0,
+                                  stream=None):
+    """The same over P partitions (z_words: (m, ceil(n/64)) uint64)."""
+    import torch
+
+    po = np.ascontiguousarray(part_of, dtype=np.uint8)
+    zz = np.ascontiguousarray(z_words, dtype=np.uint64).reshape(-1, (n + 63) // 64)
+    pl = np.ascontiguousarray(parts, dtype=np.uint64)
+    out = np.zeros(2 * zz.shape[0], dtype=np.float64)
+    s = ctypes.c_int(0)
+    st = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+    _check(lib().sv_cut_amplitudes_multi_parts(_text(circuit), n, po.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                                               int(po.max()) + 1, form, nparts_log2, pl.size,
+                                               pl.ctypes.data_as(_u64p), zz.shape[0], zz.ctypes.data_as(_u64p),
+                                               _dptr(out), ctypes.byref(s), _vp(st)), "sv_cut_amplitudes_multi_parts")
     return out.view(np.complex128).copy(), s.value
 
 
@@ -227,6 +302,27 @@ class Plan:
         arr = (_vp * len(events))(*[_vp(e.cuda_event) for e in events])
         _check(lib().sv_plan_execute_timed(self.handle, arr, len(events)), "sv_plan_execute_timed")
 
+    def tuning(self) -> dict:
+        """SV_MODE_AUTO: the measured candidates and the choice ({} otherwise)."""
+        import json
+
+        ln = ctypes.c_size_t(0)
+        _check(lib().sv_plan_tuning(self.handle, None, 0, ctypes.byref(ln)), "sv_plan_tuning")
+        buf = ctypes.create_string_buffer(ln.value + 1)
+        _check(lib().sv_plan_tuning(self.handle, buf, ln.value + 1, ctypes.byref(ln)), "sv_plan_tuning")
+        return json.loads(buf.value.decode()) if ln.value else {}
+
+    def launch_stats(self):
+        """[(FP32 lane operations per amplitude, register segments)] for every
+        launch (compiled tile passes; (0, 0) for other launches)."""
+        out = []
+        ops, seg = ctypes.c_double(), ctypes.c_int64()
+        for i in range(self.passes):
+            _check(lib().sv_plan_launch_stats(self.handle, i, ctypes.byref(ops), ctypes.byref(seg)),
+                   "sv_plan_launch_stats")
+            out.append((ops.value, seg.value))
+        return out
+
     def launch_info(self):
         """[(kernel name, algorithmic bytes)] for every launch of one execution."""
         out = []
@@ -247,6 +343,51 @@ class Plan:
             self.free()
         except Exception:
             pass
+
+
+class Batch:
+    """Independent circuits on their own states run together (sv_batch_*):
+    each member is its own chain of launches in one CUDA graph."""
+
+    def __init__(self, states, circuits):
+        if len(states) != len(circuits):
+            raise ValueError("one circuit per state")
+        self.states = list(states)
+        self._texts = [_text(c) for c in circuits]
+        hs = (_vp * len(states))(*[s.handle for s in states])
+        ts = (ctypes.c_char_p * len(states))(*self._texts)
+        self.handle = _vp()
+        _check(lib().sv_batch_create(hs, ts, len(states), ctypes.byref(self.handle)), "sv_batch_create")
+        self.info()
+
+    def info(self):
+        g, n, b, u = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_double(), ctypes.c_int()
+        _check(lib().sv_batch_info(self.handle, ctypes.byref(g), ctypes.byref(n), ctypes.byref(b), ctypes.byref(u)),
+               "sv_batch_info")
+        self.gates, self.launches, self.bytes, self.uses_graph = g.value, n.value, b.value, bool(u.value)
+        return self
+
+    def execute(self) -> None:
+        _check(lib().sv_batch_execute(self.handle), "sv_batch_execute")
+
+    def free(self) -> None:
+        if self.handle:
+            _check(lib().sv_batch_free(self.handle), "sv_batch_free")
+            self.handle = _vp()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def sv_run_batch(states, circuits) -> None:
+    """Run each circuit on its state, all members together, once."""
+    texts = [_text(c) for c in circuits]
+    hs = (_vp * len(states))(*[s.handle for s in states])
+    ts = (ctypes.c_char_p * len(states))(*texts)
+    _check(lib().sv_run_batch(hs, ts, len(states)), "sv_run_batch")
 
 
 class StateVector:

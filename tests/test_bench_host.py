@@ -98,3 +98,25 @@ int host_fn(int x) { return x + 1; }
     assert h(base.replace("2 * x", "3 * x")) != ref                          # a helper it calls
     assert h(base.replace("kW = 4", "kW = 5")) != ref                        # a constant it uses
     assert h(base, "#pragma once\nstruct Args { long n; };\nconstexpr int kUnused = 3;\n") != ref  # header struct
+
+
+def test_cut_count_of_the_42_qubit_grid():
+    """S(depth) of the 6x7 grid cut between rows 2 and 3, as the bench
+    states it (+7 per six layers), equals the library's count of decomposed
+    gates (a host-only call: no bit strings, no device work)."""
+    import ctypes
+
+    import numpy as np
+
+    from paper_1912_03243_gb300 import sv
+
+    L = sv.lib()
+    mask = C.grid_partition_mask(6, 7, 3)
+    z = np.zeros(1, dtype=np.uint64)
+    out = np.zeros(2)
+    for depth in range(1, 26):
+        c = C.grid_circuit(6, 7, depth, 1)
+        s = ctypes.c_int(-1)
+        r = L.sv_cut_amplitudes_part(c.text().encode(), 42, ctypes.c_uint64(mask), 0, ctypes.c_uint64(0), 16, 0,
+                                     z.ctypes.data_as(sv._u64p), out.ctypes.data_as(sv._dp), ctypes.byref(s), None)
+        assert r == 0 and s.value == bench.cut_gates_42q(depth), depth

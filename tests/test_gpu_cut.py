@@ -5,6 +5,7 @@ amplitudes; the 48-qubit 6x8 grid workload with both decompositions.
 Tolerance: max |d amp| <= 1e-5 * max |amp| (complex64 halves, FP64 sum)."""
 
 import math
+import os
 
 import numpy as np
 import pytest
@@ -180,6 +181,62 @@ def test_parts_add_up(S, orc, form):
     assert np.all(far == 0)
     with pytest.raises(S.SVError):
         S.sv_cut_amplitudes_part(c, c.n, mask, z, 4, 2, form=form)
+
+
+@pytest.mark.parametrize("form", [0, 1])
+def test_part_lists_sum_on_the_device(S, orc, form):
+    """sv_cut_amplitudes_parts: a rank's share (the parts p = r mod W of
+    2^ceil(log2 W)) summed by the library equals the oracle's parts added up;
+    the shares of all ranks add up to the full Eq. 3 sum; a list with a
+    repeated or out-of-range part is an argument error."""
+    from paper_1912_03243_gb300 import sharding
+
+    c = C.grid_circuit(4, 3, 12, 3)
+    mask = C.grid_partition_mask(4, 3, 2)
+    z = np.arange(1 << c.n, dtype=np.uint64)
+    full, s = S.sv_cut_amplitudes(c, c.n, mask, z, form=form)
+    for world in (1, 2, 3, 5):
+        acc = np.zeros_like(full)
+        for rank in range(world):
+            p, parts = sharding.parts_for_rank(rank, world)
+            got, sp = S.sv_cut_amplitudes_parts(c, c.n, mask, z, p, parts, form=form)
+            ref = sum(orc.cut_amplitudes_part(c, mask, z, part, p, form=form)[0] for part in parts)
+            assert sp == s
+            close(got, ref)
+            acc += got
+        close(acc, full)
+    # all parts of a split that bounds memory, in one call
+    got, _ = S.sv_cut_amplitudes_parts(c, c.n, mask, z, 3, list(range(8)), form=form)
+    close(got, full)
+    for bad in ([1, 1], [0, 4], []):
+        with pytest.raises(S.SVError):
+            S.sv_cut_amplitudes_parts(c, c.n, mask, z, 2, bad, form=form)
+
+
+def test_sharded_library_sum_two_ranks(S, orc, tmp_path):
+    """Two gloo ranks on the one GPU: each sums its branch parts with the
+    library, one host all-reduce combines them; equals the oracle's Eq. 3
+    sum."""
+    import socket
+    import sys
+
+    import torch.multiprocessing as mp
+
+    sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+    import mp_helpers
+
+    c = C.grid_circuit(4, 3, 12, 5)
+    mask = C.grid_partition_mask(4, 3, 2)
+    z = C.random_bitstrings(300, c.n, 3)
+    sock = socket.socket()
+    sock.bind(("127.0.0.1", 0))
+    port = sock.getsockname()[1]
+    sock.close()
+    out = tmp_path / "lib_sum.npy"
+    mp.start_processes(mp_helpers.sharded_library_sum, args=(2, port, c.text(), c.n, mask, [int(v) for v in z], 0,
+                                                             str(out)), nprocs=2, start_method="spawn", join=True)
+    full, _ = orc.cut_amplitudes(c, mask, z)
+    close(np.load(out), full)
 
 
 @pytest.mark.parametrize("form", [0, 1])
