@@ -219,41 +219,60 @@ def workload(args):
 
 # ----------------------------------------------------------------- CPU oracle
 
-def oracle_sample(args, budget_s: float, min_s: float = 10.0):
-    """Time the CPU oracle (single thread, complex128) on successive layers of
-    the same circuit family at a smaller qubit count; gates/s is scaled to
-    args.n by 2^(n_sample - n) (the oracle's cost per gate is proportional to
-    2^n).  Returns (gates/s at args.n, description, seconds)."""
-    import oracle
+def oracle_layers(n, depth, seed):
+    """The random circuit of the benchmark family at n qubits, split into its
+    layers (n single-qubit gates, then that layer's CZs)."""
     from paper_1912_03243_gb300 import circuits as C
 
-    ns = min(args.n, 26)
-    full = C.random_circuit(ns, args.depth, args.seed)
-    # split into layers: ns single-qubit gates followed by that layer's CZs
+    full = C.random_circuit(n, depth, seed)
     gates, per_layer, i = full.gates, [], 0
-    for _ in range(args.depth):
+    for _ in range(depth):
         start = i
-        i += ns
+        i += n
         while i < len(gates) and gates[i][0] == "CZ":
             i += 1
-        c = C.Circuit(ns)
+        c = C.Circuit(n)
         c.gates = gates[start:i]
         per_layer.append(c)
-    psi = oracle.basis_state(ns)
+    return per_layer
+
+
+def oracle_point(n, depth, seed, budget_s: float, min_s: float):
+    """Gates/s of the CPU oracle (single thread, complex128) on successive
+    layers of the family at n qubits, layer by layer until min_s of work."""
+    import oracle
+
+    psi = oracle.basis_state(n)
     done, t_used = 0, 0.0
-    for c in per_layer:
+    for c in oracle_layers(n, depth, seed):
         t0 = time.perf_counter()
         psi = oracle.run(c, psi=psi)
         t_used += time.perf_counter() - t0
         done += len(c)
         if t_used >= min_s or t_used >= budget_s:
             break
-    gps_sample = done / t_used
-    scaled = gps_sample * 2.0 ** (ns - args.n)
-    desc = (f"oracle (plain C, complex128, 1 thread) on the first {done} gates of the same circuit family at "
-            f"{ns} qubits ({(16 << ns) >> 20} MiB): {gps_sample:.2f} gates/s, scaled by 2^({ns}-{args.n}) to "
-            f"{args.n} qubits")
-    return scaled, desc, t_used
+    return done / t_used, done, t_used
+
+
+def oracle_sample(args, budget_s: float, min_s: float = 10.0, ns=None):
+    """Time the CPU oracle at one or more qubit counts below args.n and scale
+    each to args.n by 2^(n_sample - n) (its cost per gate is proportional to
+    the amplitude count; the spread of the scaled values checks that).  The
+    value is the point at the largest n.  Returns (gates/s at args.n,
+    description, seconds, points)."""
+    ns = ns or [min(args.n, 26)]
+    points = []
+    for n in ns:
+        gps, done, t = oracle_point(n, args.depth, args.seed, budget_s / len(ns), min_s / len(ns))
+        points.append({"n": n, "gates": done, "s": round(t, 3), "gates_per_s": gps,
+                       "scaled_to_n": gps * 2.0 ** (n - args.n)})
+    top = points[-1]
+    desc = (f"oracle (plain C, complex128, 1 thread of {os.cpu_count()} host cores) on the first layers of the same "
+            f"circuit family at n = {', '.join(str(p['n']) for p in points)} qubits, each scaled by 2^(n-{args.n}) "
+            f"to {args.n} qubits: " + ", ".join(f"{p['gates_per_s']:.3g} gates/s at {p['n']} -> "
+                                                f"{p['scaled_to_n']:.3g}" for p in points)
+            + f"; value from n = {top['n']}")
+    return top["scaled_to_n"], desc, sum(p["s"] for p in points), points
 
 
 def run_reference(args, world, rank):
@@ -263,7 +282,7 @@ def run_reference(args, world, rank):
     per_step = []
     desc = None
     for k in range(args.warmup + args.steps):
-        v, desc, t = oracle_sample(args, budget_s=8.0, min_s=2.0)
+        v, desc, t, _ = oracle_sample(args, budget_s=8.0, min_s=2.0)
         if k >= args.warmup:
             per_step.append((v, t))
     value = statistics.median([v for v, _ in per_step])
@@ -272,7 +291,8 @@ def run_reference(args, world, rank):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median([t for _, t in per_step]),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": workload(args)[1], "n": args.n, "depth": args.depth},
-        "cpu_baseline": {"value": value, "unit": "gates/s", "cores": 1, "kind": "oracle", "sample": desc},
+        "cpu_baseline": {"value": value, "unit": "gates/s", "cores": 1, "host_cores": os.cpu_count(),
+                         "kind": "oracle", "sample": desc},
         "e2e": {"value": value, "unit": "gates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -1081,8 +1101,10 @@ def run_ours(args, world, rank, local):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, sdesc, tcpu = oracle_sample(args, budget_s=30.0)
-        cpu = {"value": v, "unit": "gates/s", "cores": 1, "kind": "oracle", "sample": sdesc}
+        ns = [m for m in (20, 24, 26, 28) if m <= args.n]
+        v, sdesc, tcpu, pts = oracle_sample(args, budget_s=40.0, min_s=24.0, ns=ns)
+        cpu = {"value": v, "unit": "gates/s", "cores": 1, "host_cores": os.cpu_count(), "kind": "oracle",
+               "sample": sdesc, "points": pts}
 
     plan.free()
     extras = None

@@ -136,10 +136,84 @@ std::vector<PGate> lower_for_tiles(const Circuit &c) {
 
 namespace {
 
+// Shared-memory bank model of the complex64 passes: 8-byte amplitude j of a
+// tile lives at element (swz(j >> 1) << 1) | (j & 1), swz(c) = c ^ ((c >> 3 ^
+// c >> 6 ^ c >> 9) & 7), the XOR swizzle of the generated kernels.  A warp's
+// 8-byte accesses are served per half-warp (lanes 0-15, 16-31); the wavefronts
+// of a half-warp are the most distinct 4-byte words any bank receives.  The
+// swizzle is linear over XOR, so a register slot's constant offset permutes
+// the banks without changing that count: it depends on the lane bits alone.
+uint32_t swz_chunk(uint32_t c) { return c ^ (((c >> 3) ^ (c >> 6) ^ (c >> 9)) & 7u); }
+
+int bank_ways64(const int lanes[5]) {
+    int worst = 0;
+    for (int half = 0; half < 2; ++half) {
+        uint32_t words[32];  // the distinct 4-byte words of this half-warp
+        int nw = 0;
+        for (int l = 0; l < 16; ++l) {
+            const int ll = l + 16 * half;
+            uint32_t j = 0;
+            for (int k = 0; k < 5; ++k)
+                if (ll >> k & 1) j |= 1u << lanes[k];
+            const uint32_t e = (swz_chunk(j >> 1) << 1) | (j & 1u);
+            for (uint32_t w = 2 * e; w < 2 * e + 2; ++w)
+                if (std::find(words, words + nw, w) == words + nw) words[nw++] = w;
+        }
+        int ways[32] = {0};
+        for (int i = 0; i < nw; ++i) worst = std::max(worst, ++ways[words[i] & 31u]);
+    }
+    return worst;
+}
+
+// Lanes of a complex64 segment: among the 5-bit subsets of the free tile
+// bits (and the choice of which one selects the half-warp) the one with the
+// fewest shared-memory wavefronts; with `hbm`, a subset holding tile bits
+// 0-2 (whole 32-byte sectors for a direct HBM access) comes first, then one
+// holding bit 3 too (whole 128-byte lines).  Warp bits follow, ascending.
+void order_thread_bits64(const std::vector<int> &avail, bool hbm, uint8_t *tpos) {
+    const int na = int(avail.size());
+    int best[5] = {0, 0, 0, 0, 0};
+    long best_score = -1;
+    for (uint32_t sub = 0; sub < (1u << na); ++sub) {
+        if (__builtin_popcount(sub) != 5 || na < 5) continue;
+        int pick[5], k = 0;
+        for (int i = 0; i < na; ++i)
+            if (sub >> i & 1) pick[k++] = avail[size_t(i)];
+        uint32_t set = 0;
+        for (int i = 0; i < 5; ++i) set |= 1u << pick[i];
+        for (int hi = 0; hi < 5; ++hi) {
+            int lanes[5], q = 0;
+            for (int i = 0; i < 5; ++i)
+                if (i != hi) lanes[q++] = pick[i];
+            lanes[4] = pick[hi];
+            const int ways = bank_ways64(lanes);
+            long score = long(16 - ways) * 4;
+            if (hbm) score += ((set & 7u) == 7u ? 1000 : 0) + ((set & 15u) == 15u ? 100 : 0);
+            score = score * 64 + (63 - pick[hi]);  // ties: the lower sets first
+            if (score > best_score) {
+                best_score = score;
+                std::copy(lanes, lanes + 5, best);
+            }
+        }
+    }
+    if (best_score < 0) {  // fewer than 5 free bits (not a complex64 layout)
+        for (int i = 0; i < na; ++i) tpos[i] = uint8_t(avail[size_t(i)]);
+        return;
+    }
+    int k = 0;
+    for (int i = 0; i < 5; ++i) tpos[k++] = uint8_t(best[i]);
+    for (int b : avail)
+        if (std::find(best, best + 5, b) == best + 5) tpos[k++] = uint8_t(b);
+}
+
 // Lane order for the thread bits of a segment: the first lane bits get tile
 // positions whose shared-memory bank contributions are independent under the
 // XOR swizzle of k_tile (see phys_chunk there), the rest ascending.
 void order_thread_bits(const std::vector<int> &avail, bool c64, uint8_t *tpos) {
+    if (c64 && avail.size() >= 5) {
+        order_thread_bits64(avail, false, tpos);
+        return;
+    }
     std::vector<int> rest = avail, lanes;
     auto take = [&](auto pred) {
         for (size_t i = 0; i < rest.size(); ++i)
@@ -720,9 +794,10 @@ sv_status plan_tiles_one(const std::vector<PGate> &G, int n, const TileConfig &c
                 uint32_t reg = 0;
                 for (int sl = 0; sl < rb; ++sl) reg |= 1u << sg.rpos[sl];
                 if ((reg & 7u) != 0 || L < 3) continue;
-                int k = 0;
+                std::vector<int> avail;
                 for (int b = 0; b < m; ++b)
-                    if (!(reg >> b & 1)) sg.tpos[k++] = uint8_t(b);
+                    if (!(reg >> b & 1)) avail.push_back(b);
+                order_thread_bits64(avail, true, sg.tpos);
             }
         }
         out->passes.push_back(pa);
