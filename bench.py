@@ -219,27 +219,23 @@ def workload(args):
 
 # ----------------------------------------------------------------- CPU oracle
 
-def oracle_layers(n, depth, seed):
-    """The random circuit of the benchmark family at n qubits, split into its
-    layers (n single-qubit gates, then that layer's CZs)."""
+def oracle_layers(n, depth, seed, chunk: int = 8):
+    """The random circuit of the benchmark family at n qubits, in order, in
+    pieces of at most `chunk` gates (the timing stops between pieces)."""
     from paper_1912_03243_gb300 import circuits as C
 
-    full = C.random_circuit(n, depth, seed)
-    gates, per_layer, i = full.gates, [], 0
-    for _ in range(depth):
-        start = i
-        i += n
-        while i < len(gates) and gates[i][0] == "CZ":
-            i += 1
+    gates = C.random_circuit(n, depth, seed).gates
+    pieces = []
+    for i in range(0, len(gates), chunk):
         c = C.Circuit(n)
-        c.gates = gates[start:i]
-        per_layer.append(c)
-    return per_layer
+        c.gates = gates[i:i + chunk]
+        pieces.append(c)
+    return pieces
 
 
 def oracle_point(n, depth, seed, budget_s: float, min_s: float):
-    """Gates/s of the CPU oracle (single thread, complex128) on successive
-    layers of the family at n qubits, layer by layer until min_s of work."""
+    """Gates/s of the CPU oracle (single thread, complex128) on the family at n
+    qubits, a few gates at a time, until min_s of work."""
     import oracle
 
     psi = oracle.basis_state(n)
@@ -267,7 +263,7 @@ def oracle_sample(args, budget_s: float, min_s: float = 10.0, ns=None):
         points.append({"n": n, "gates": done, "s": round(t, 3), "gates_per_s": gps,
                        "scaled_to_n": gps * 2.0 ** (n - args.n)})
     top = points[-1]
-    desc = (f"oracle (plain C, complex128, 1 thread of {os.cpu_count()} host cores) on the first layers of the same "
+    desc = (f"oracle (plain C, complex128, 1 thread of {os.cpu_count()} host cores) on the first gates of the same "
             f"circuit family at n = {', '.join(str(p['n']) for p in points)} qubits, each scaled by 2^(n-{args.n}) "
             f"to {args.n} qubits: " + ", ".join(f"{p['gates_per_s']:.3g} gates/s at {p['n']} -> "
                                                 f"{p['scaled_to_n']:.3g}" for p in points)
@@ -821,7 +817,7 @@ def cut_gates_42q(depth: int) -> int:
     return 7 * full + (4 if rem > 2 else 0) + (3 if rem > 3 else 0)
 
 
-def bench_cut42_depth(S, C, budget_s: float = 240.0):
+def bench_cut42_depth(S, C, budget_s: float = 200.0):
     """Decomposition at the paper's scale (Sec. 4, Fig. 4 workload shape): a
     42-qubit 6x7 grid circuit cut between rows 0-2 and 3-5 (21 + 21 qubits),
     1024 seeded amplitudes.  The branches are split into 2^p parts (p chosen
@@ -851,18 +847,22 @@ def bench_cut42_depth(S, C, budget_s: float = 240.0):
             t0 = time.perf_counter()
             S.sv_cut_amplitudes_parts(c, n, mask, z, plog, [0], form=form)  # compiles, runs one part
             torch.cuda.synchronize()
+            tpart = time.perf_counter()
+            if len(parts) > 1:  # one compiled part, for the projection
+                S.sv_cut_amplitudes_parts(c, n, mask, z, plog, [1], form=form)
+                torch.cuda.synchronize()
             t1 = time.perf_counter()
-            est = (t1 - t0) * len(parts)
+            est = (t1 - tpart) * len(parts)
             if depth > 14 and spent + est > budget_s:
                 rows[depth] = {"gates": len(c), "cut_gates": s, "parts": len(parts),
-                               "skipped": f"projected {est:.0f} s (one part with its compile x {len(parts)}) "
-                                          f"exceeds the remaining budget"}
+                               "skipped": f"projected {est:.0f} s (one compiled part x {len(parts)}) exceeds the "
+                                          f"remaining budget of {budget_s - spent:.0f} s"}
                 break
             a, _ = S.sv_cut_amplitudes_parts(c, n, mask, z, plog, parts, form=form)
             torch.cuda.synchronize()
             t = time.perf_counter() - t1
             spent += time.perf_counter() - t0
-            res[form] = (a, t, t1 - t0)
+            res[form] = (a, t, tpart - t0)
         if 0 not in res:
             continue
         a0, t, tc = res[0]

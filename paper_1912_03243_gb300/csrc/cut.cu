@@ -29,6 +29,9 @@
 // P partitions' amplitudes and the sum in FP64, times the weight.
 #include <complex>
 #include <cstdlib>
+#include <mutex>
+#include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "plan.h"
@@ -187,9 +190,55 @@ bool prefix_sharing() {
     return !(e && e[0] == '0');
 }
 
+// Schedules by partition content (its gates, sizes, branch-bit count and the
+// code-generation settings): a repeated decomposition skips the planning, and
+// the compiled passes it names stay loaded for the process.
+std::mutex g_sched_mu;
+std::unordered_map<std::string, std::pair<bool, std::vector<HalfStep>>> g_sched;
+constexpr size_t kSchedCacheMax = 256;
+
+std::string schedule_key(const Half &h, int S) {
+    std::string k = std::to_string(h.nlocal) + "," + std::to_string(h.nq) + "," + std::to_string(S) + "," +
+                    std::to_string(int(prefix_sharing())) + "," + tile_config_name(tile_config64()) + "," +
+                    tile_codegen_key() + "," + std::to_string(plan_lookahead_width()) + "|";
+    int dev = 0;
+    cudaGetDevice(&dev);
+    k += std::to_string(dev) + "|";
+    for (const PGate &g : h.gates) {
+        k.append(reinterpret_cast<const char *>(&g.kind), sizeof g.kind);
+        k.append(reinterpret_cast<const char *>(&g.target), sizeof g.target);
+        k.append(reinterpret_cast<const char *>(&g.cmask), sizeof g.cmask);
+        k.append(reinterpret_cast<const char *>(&g.cval), sizeof g.cval);
+        k.append(reinterpret_cast<const char *>(g.u), sizeof g.u);
+        k.append(reinterpret_cast<const char *>(&g.scale), sizeof g.scale);
+    }
+    return k;
+}
+
+sv_status plan_half_uncached(Half &h, int S);
+
 // The schedule of a partition: planned and compiled once, then run for every
 // branch part (the fixed branch bits of a part are launch parameters).
 sv_status plan_half(Half &h, int S) {
+    const std::string key = schedule_key(h, S);
+    {
+        std::lock_guard<std::mutex> lock(g_sched_mu);
+        auto it = g_sched.find(key);
+        if (it != g_sched.end()) {
+            h.init_all = it->second.first;
+            h.steps = it->second.second;
+            return SV_OK;
+        }
+    }
+    const sv_status s = plan_half_uncached(h, S);
+    if (s) return s;
+    std::lock_guard<std::mutex> lock(g_sched_mu);
+    if (g_sched.size() >= kSchedCacheMax) g_sched.clear();
+    g_sched[key] = std::make_pair(h.init_all, h.steps);
+    return SV_OK;
+}
+
+sv_status plan_half_uncached(Half &h, int S) {
     h.steps.clear();
     h.init_all = !prefix_sharing();
     if (h.init_all) return plan_stage(&h.steps, h.gates, h.nq);
