@@ -5,8 +5,10 @@
 // Real expansion: with amplitudes interleaved (re, im), the complex block U
 // acts as the 2d x 2d real matrix Ut, Ut[2r+a][2c+b] = [[Re, -Im], [Im, Re]]
 // of U[r][c] (d = 2^k).  A = I_P (x) Ut (P = 64/d copies on the diagonal) is
-// always 128 x 128, so one MMA shape (M = N = 128, K = 16 per instruction)
-// serves every k <= 6; column n of B holds P groups of d amplitudes.
+// always 128 x 128, so one MMA shape (M = 128, N = kTcN = 64, K = 16 per
+// instruction) serves every k <= 6; column n of B holds P groups of d
+// amplitudes.  For k < 6 most of each product multiplies zeros: harmless
+// while the kernel is bound by HBM.
 //
 // Split precision: A = Ah + Al and B = Bh + Bl with BF16 parts (Ah = bf16(A),
 // Al = bf16(A - Ah)); D = Ah Bh + Ah Bl + Al Bh accumulates in FP32 in tensor
@@ -15,18 +17,18 @@
 // Per CTA (persistent, one per SM, two groups of 256 threads): A lives in
 // tensor memory (row m in lane m, two BF16 K elements per 32-bit column; A_hi
 // in columns 0-63, A_lo in 64-127, written once), which leaves shared memory
-// to the groups: each has its own B operand, two FP32 staging tiles, 64 TMEM
-// accumulator columns, mbarrier and named barrier.  Per tile of 2^12
-// amplitudes (the k block qubits plus the lowest other qubits; B is 128 x 64)
-// and group:
-//   the tile's cp.async was issued one tile earlier into one staging tile,
-//   the next tile's goes into the other now -> convert to Bh, Bl in the
-//   K-major no-swizzle canonical layout -> one thread issues 3 x 8
-//   tcgen05.mma (A from tensor memory, M = 128, N = 64, K = 16 each) and
-//   commits to the group's mbarrier -> the group waits (bounded by
-//   %globaltimer) -> each warp reads its 32 TMEM lanes with tcgen05.ld and
-//   scatters FP32 results back to the staging tile -> coalesced 16-byte
-//   stores to HBM.
+// to the groups: each has its own B operand, a ring of kTcRing FP32 staging
+// tiles, 64 TMEM accumulator columns, mbarrier and named barrier.  Per tile
+// of 2^12 amplitudes (the k block qubits plus the lowest other qubits; B is
+// 128 x 64) and group:
+//   the tile's cp.async was issued kTcRing - 1 tiles earlier into its ring
+//   slot, and the load kTcRing - 1 tiles ahead goes into the slot freed by
+//   the previous tile now (kTcRing - 1 loads in flight per group) -> convert
+//   to Bh, Bl in the K-major no-swizzle canonical layout -> one thread issues
+//   3 x 8 tcgen05.mma (A from tensor memory) and commits to the group's
+//   mbarrier -> the group waits (bounded by %globaltimer) -> each warp reads
+//   its 32 TMEM lanes with tcgen05.ld and scatters FP32 results back to the
+//   staging tile -> coalesced 16-byte stores to HBM.
 // Timeout: the wait for the MMAs is bounded by %globaltimer.  When it runs
 // out, the group stops, the CTA frees its tensor memory and the host sees
 // SV_ERR_TIMEOUT.  The test hook (skip_mma) issues no MMA, so nothing is in
@@ -54,11 +56,16 @@ constexpr int kTcGroup = 256;                  // threads of one group
 constexpr int kTcGroups = 2;                   // groups (tiles in flight) per CTA
 constexpr int kTcThreads = kTcGroups * kTcGroup;
 constexpr int kTcACols = 64;                   // TMEM columns of one 128 x 128 BF16 A operand
-constexpr int kTcCols = 2 * kTcACols + kTcGroups * kTcN;  // A_hi, A_lo, one accumulator per group (256)
-static_assert(kTcCols == 256, "tensor memory allocation is a power of two");
+// A_hi, A_lo and one accumulator per group, in an allocation of a power of two
+constexpr int kTcCols = 256;
+static_assert(2 * kTcACols + kTcGroups * kTcN <= kTcCols, "tensor memory allocation");
 constexpr uint32_t kOpBytes = 128 * 128 * 2;   // one BF16 A operand image (32 KiB)
 constexpr uint32_t kBBytes = kTcN * 128 * 2;   // one BF16 B operand (16 KiB)
 constexpr uint32_t kStageBytes = (1u << kTcM) * 8;  // one FP32 staging tile (32 KiB)
+// staging tiles per group (kTcRing - 1 loads in flight); two fill the shared
+// memory of two groups.  (2^11-amplitude tiles with a ring of five measured
+// slower: the per-tile MMA round trip then dominates.)
+constexpr int kTcRing = 2;
 constexpr int kChunkIters = (1 << kTcM) / 2 / kTcGroup;  // 16-byte chunks per thread and tile
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return uint32_t(__cvta_generic_to_shared(p)); }
@@ -68,6 +75,11 @@ __device__ __forceinline__ void cp_async16(uint32_t saddr, const void *g) {
 }
 __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+// commit this thread's copies issued since the last commit as one group, then
+// wait until at most kTcRing - 1 groups (the newest) are still in flight
+__device__ __forceinline__ void cp_async_commit_wait_ring() {
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group %0;\n" ::"n"(kTcRing - 1) : "memory");
 }
 // barrier of one 256-thread group (named barrier 1 + g)
 __device__ __forceinline__ void group_sync(int g) { asm volatile("bar.sync %0, 256;\n" ::"r"(1 + g) : "memory"); }
@@ -166,9 +178,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fused_tc(float2 *__restrict__
     __shared__ uint16_t sHi[kChunkIters];                  // swizzled chunk of the chunk bits above 7
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int g = tid / kTcGroup, lt = tid % kTcGroup, gw = warp & 7;  // group, thread and warp in the group
-    unsigned char *gbase = smem + size_t(g) * (2 * kBBytes + 2 * kStageBytes);
+    unsigned char *gbase = smem + size_t(g) * (2 * kBBytes + kTcRing * kStageBytes);
     unsigned char *sBh = gbase, *sBl = gbase + kBBytes;
-    unsigned char *sStage = gbase + 2 * kBBytes;  // two FP32 staging tiles of 2^kTcM amplitudes
+    unsigned char *sStage = gbase + 2 * kBBytes;  // kTcRing FP32 staging tiles of 2^kTcM amplitudes
     const uint32_t mbar_a = smem_u32(&mbar[g]);
 
     for (int i = tid; i < 64; i += kTcThreads) {
@@ -264,15 +276,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fused_tc(float2 *__restrict__
     int buf = 0;
     const uint64_t stride = uint64_t(kTcGroups) * gridDim.x;
     const uint64_t first = uint64_t(kTcGroups) * blockIdx.x + uint64_t(g);
-    // one cp.async group per tile: wait_group 1 leaves only the newest (the
-    // next tile's) in flight
-    if (first < a.ntiles) load_tile(first, 0);
-    asm volatile("cp.async.commit_group;\n" ::: "memory");
-    for (uint64_t tile = first; tile < a.ntiles; tile += stride, buf ^= 1) {
-        // the other staging tile was stored before the last iteration's
-        // closing barrier
-        if (tile + stride < a.ntiles) load_tile(tile + stride, buf ^ 1);
-        asm volatile("cp.async.commit_group;\ncp.async.wait_group 1;\n" ::: "memory");
+    // a ring of kTcRing staging tiles: the loads of the next kTcRing - 1
+    // tiles are in flight while one is converted, multiplied, read back and
+    // stored; one cp.async group per tile (an empty group past the end)
+    for (int r = 0; r < kTcRing - 1; ++r) {
+        const uint64_t tt = first + uint64_t(r) * stride;
+        if (tt < a.ntiles) load_tile(tt, r);
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    }
+    for (uint64_t tile = first; tile < a.ntiles; tile += stride, buf = buf + 1 == kTcRing ? 0 : buf + 1) {
+        // the staging tile before this one in the ring was stored before the
+        // last iteration's closing barrier: it takes the load kTcRing - 1 ahead
+        const uint64_t ahead = tile + uint64_t(kTcRing - 1) * stride;
+        if (ahead < a.ntiles) load_tile(ahead, buf == 0 ? kTcRing - 1 : buf - 1);
+        cp_async_commit_wait_ring();
         group_sync(g);
         float2 *sX = reinterpret_cast<float2 *>(sStage + buf * kStageBytes);
         const uint64_t base = tile_base(tile);
@@ -468,7 +485,7 @@ cudaError_t tc_launch(sv_state *h, const TcArgs &args, const void *dA) {
         const cudaError_t e = ensure_err_word(h);
         if (e != cudaSuccess) return e;
     }
-    const size_t smem = kTcGroups * (2 * size_t(kBBytes) + 2 * size_t(kStageBytes));
+    const size_t smem = kTcGroups * (2 * size_t(kBBytes) + kTcRing * size_t(kStageBytes));
     static std::atomic<uint64_t> configured{0};
     if (attrs_needed(configured, h->device)) {
         const cudaError_t e = cudaFuncSetAttribute(k_fused_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));

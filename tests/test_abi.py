@@ -167,3 +167,29 @@ def test_planner_does_not_regress(L, name, n, gates, passes, segments):
     g, p, s = sv.sv_plan_stats(c, n, "c64")
     assert g == gates
     assert p <= passes and s <= segments, (p, s)
+
+
+def test_direct_hbm_segments_cover_whole_sectors(L):
+    """Host only: in the generated passes of the 28-qubit depth-24 benchmark
+    family, every register segment that loads from or stores to HBM directly
+    has lanes on global qubits 0, 1 and 2 (8 lanes x 8 contiguous bytes: whole
+    32-byte sectors per warp access), and every pass starts with such a load
+    or with the staged copy."""
+    import re
+
+    c = C.random_circuit(28, 24, 1)
+    _, passes, _ = sv.sv_plan_stats(c, 28, "c64")
+    direct = 0
+    for i in range(passes):
+        src = sv.sv_plan_pass_source(c, 28, "c64", i)
+        assert ("psi[gq + " in src) or ("cpa16(smem" in src), i
+        for block in src.split("u64 gq = 0;")[1:]:
+            lanes = set()
+            for m in re.finditer(r"gq \|= \(\(u64\)\(\(t >> (\d+)\) & (\d+)ull\)\) << (\d+);", block[:1200]):
+                k, mask, p = int(m.group(1)), int(m.group(2)), int(m.group(3))
+                for b in range(mask.bit_length()):
+                    if k + b < 5:
+                        lanes.add(p + b)
+            assert {0, 1, 2} <= lanes, (i, sorted(lanes))
+            direct += 1
+    assert direct >= passes  # most passes load and store directly

@@ -63,12 +63,13 @@ def test_blocks_14q(S, orc, k):
         check_c64(s.to_numpy(), orc.apply_kq(psi0, qs, u))
 
 
-@pytest.mark.parametrize("n", [12, 13, 14, 20])
+@pytest.mark.parametrize("n", [12, 13, 14, 20, 22])
 def test_blocks_one_and_many_tiles(S, orc, n):
-    """Tiles hold 2^12 amplitudes and each CTA keeps two in flight (one per
-    thread group): n = 12 is one tile (one group idle), n = 13 two (one CTA,
-    both groups busy once), n = 14 four, n = 20 gives 256 tiles, so the
-    groups loop over several tiles (mbarrier phases alternate)."""
+    """Tiles hold 2^12 amplitudes; each CTA has two thread groups, each with
+    a ring of staging tiles (the next tile's load in flight): n = 12 is one
+    tile (one group idle), n = 13 two (one CTA, both groups busy once), n =
+    14 four, n = 20 gives 256 tiles, n = 22 1024 (three or four per group:
+    the ring wraps, mbarrier phases alternate)."""
     rng = np.random.default_rng(n)
     psi0 = C.random_state(n, 7 + n)
     s = S.StateVector(n, "c64")
