@@ -51,6 +51,9 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the two-byte-code (35 qubits) and decomposition (48 qubits) measurements")
+    ap.add_argument("--cut42-budget", type=float, default=60.0,
+                    help="seconds the 42-qubit depth sweep may spend on depths 15-16 (S = 18, 21); a depth whose "
+                         "projected time exceeds what is left is reported as skipped")
     ap.add_argument("--profile-case", default=None, choices=sorted(PROFILE_CASES),
                     help="run one small fixed invocation of a kernel family for a profiler capture, then exit")
     return ap.parse_args()
@@ -817,7 +820,7 @@ def cut_gates_42q(depth: int) -> int:
     return 7 * full + (4 if rem > 2 else 0) + (3 if rem > 3 else 0)
 
 
-def bench_cut42_depth(S, C, budget_s: float = 200.0):
+def bench_cut42_depth(S, C, budget_s: float = 60.0):
     """Decomposition at the paper's scale (Sec. 4, Fig. 4 workload shape): a
     42-qubit 6x7 grid circuit cut between rows 0-2 and 3-5 (21 + 21 qubits),
     1024 seeded amplitudes.  The branches are split into 2^p parts (p chosen
@@ -1116,7 +1119,7 @@ def run_ours(args, world, rank, local):
                   "qft_32q": bench_qft(S, C, hbm_peak), "h_sweep_32q": bench_h_sweep(S, C, hbm_peak, peak_kind),
                   "random_30q": bench_30q(S, C, hbm_peak), "expect_32q": bench_expect(S, C, hbm_peak),
                   "ghz_sweep": bench_ghz_sweep(S, C), "batch_64": bench_batch(S, C),
-                  "cut_42q_depth": bench_cut42_depth(S, C),
+                  "cut_42q_depth": bench_cut42_depth(S, C, args.cut42_budget),
                   "ghz128_m2e27": bench_ghz128(S, C)}
     if rank == 0:
         line = {

@@ -261,8 +261,9 @@ std::vector<Strategy> candidates(const sv_state *h) {
     if (h->n >= tile_m) {
         if (h->dt == SV_C64) {
             // the generator's register bits, CTAs per SM and HBM I/O forms
-            const int opts[][3] = {{5, 2, 1}, {5, 2, 0}, {4, 2, 1}, {5, 3, 1}};
-            for (const auto &o : opts) v.push_back(Strategy{SV_MODE_TILED, tile_config64(o[0], o[1], o[2]), 0});
+            const int opts[][4] = {{5, 2, 1, 0}, {5, 2, 1, 1}, {5, 2, 0, 0}, {4, 2, 1, 0}, {5, 3, 1, 0}};
+            for (const auto &o : opts)
+                v.push_back(Strategy{SV_MODE_TILED, tile_config64(o[0], o[1], o[2], o[3]), 0});
         } else {
             v.push_back(Strategy{SV_MODE_TILED, tile_config128(), 0});
         }

@@ -94,6 +94,7 @@ struct TileConfig {
     bool c64;
     int ctas = 2;        // CTAs per SM the passes are compiled for (register budget)
     bool direct = true;  // complex64: first / last segment straight between HBM and registers
+    bool prefetch = false;  // complex64: persistent CTAs copy the next tile during the last segment
 };
 
 template <typename R>
@@ -101,6 +102,7 @@ struct TilePlan {
     int m = 0, rb = 0;  // tile bits, register bits per thread
     int ctas = 2;
     bool direct = true;
+    bool prefetch = false;
     std::vector<TilePassArgs> passes;
     std::vector<TileOp<R>> ops;
     std::vector<TileSeg> segs;
@@ -159,7 +161,7 @@ int tile_ctas_per_sm();
 // The tile configuration of complex64 / complex128 passes: the environment's
 // defaults, or the given register bits, CTAs per SM and direct I/O (an
 // autotuner's candidate; 0 / -1 keep the default).
-TileConfig tile_config64(int rb = 0, int ctas = 0, int direct = -1);
+TileConfig tile_config64(int rb = 0, int ctas = 0, int direct = -1, int prefetch = -1);
 TileConfig tile_config128();
 // Folder of the compiled-pass disk cache ("" when there is none).
 std::string jit_cache_dir();

@@ -117,6 +117,7 @@ bool packed_adds_enabled() {
 struct HbmIo {
     bool load, store;
     int nseg;
+    bool prefetch;  // persistent CTAs; the next tile's copy overlaps the last segment
 };
 
 template <typename R>
@@ -136,7 +137,12 @@ HbmIo hbm_io(const TilePlan<R> &tp, size_t pass) {
         for (int k = 0; k < 5 && k < tp.m - tp.rb; ++k) lanes |= 1u << sg.tpos[k];
         return (lanes & 7u) == 7u && pa.lc >= 3;
     };
-    return HbmIo{on && contiguous(first), on && contiguous(last), nseg};
+    // prefetch form: the last segment stores straight to HBM, so shared memory
+    // is free from its gather on and takes the next tile's copy; the first
+    // segment then gathers the copied tile from shared memory
+    const bool store = on && contiguous(last);
+    const bool prefetch = tp.prefetch && store && first >= 0;
+    return HbmIo{on && contiguous(first) && !prefetch, store, nseg, prefetch};
 }
 
 template <typename R>
@@ -185,15 +191,34 @@ std::string gen_pass(const TilePlan<R> &tp, size_t pass) {
     int tpos[kTileMaxQ];
     for (int k = 0; k < tbits; ++k) tpos[k] = pa.tile_pos[k + G.EPC_LOG];
     o << "extern \"C\" __global__ void __launch_bounds__(" << G.NT << ", " << tp.ctas << ") svp(" << C2T
-      << "* __restrict__ psi, const u64 prm) {\n";
+      << "* __restrict__ psi, const u64 prm, const u64 ntiles) {\n";
     o << "  extern __shared__ __align__(16) unsigned char smem[];\n";
     o << "  " << C2T << "* sm = reinterpret_cast<" << C2T << "*>(smem);\n";
-    // the CTA index is the tile number; conditions on outer qubits test
-    // its bits, and the global offsets are recomputed for the store
-    // (short live ranges leave the registers to the amplitudes)
-    o << "  const u32 t = threadIdx.x;\n  const u64 cta = blockIdx.x;\n";
+    // the CTA index is the tile number (persistent CTAs: the loop variable);
+    // conditions on outer qubits test its bits, and the global offsets are
+    // recomputed for the store (short live ranges leave the registers to the
+    // amplitudes)
+    o << "  const u32 t = threadIdx.x;\n";
     const HbmIo io = hbm_io(tp, pass);
-    if (!io.load) {
+    // the 16-byte copies of tile `tv` into the swizzled shared tile
+    auto emit_tile_copy = [&](const char *tv) {
+        o << "  {\n  u64 g0 = 0;\n";
+        emit_deposit(o, "g0", tv, opos, pa.nouter, "u64");
+        emit_deposit(o, "g0", "t", tpos, tbits, "u64");
+        o << "  const u32 s0 = swz(t);\n";
+        for (int i = 0; i < iters; ++i)
+            o << "  cpa16(smem + ((s0 ^ " << si[size_t(i)] << "u) << 4), psi + (g0 | " << gi[size_t(i)] << "ull));\n";
+        o << "  asm volatile(\"cp.async.commit_group;\\n\" ::: \"memory\");\n  }\n";
+    };
+    if (io.prefetch) {
+        o << "  if (u64(blockIdx.x) >= ntiles) return;\n";
+        emit_tile_copy("u64(blockIdx.x)");
+        o << "  for (u64 cta = blockIdx.x; cta < ntiles; cta += gridDim.x) {\n";
+        o << "  asm volatile(\"cp.async.wait_group 0;\\n\" ::: \"memory\");\n  __syncthreads();\n";
+    } else {
+        o << "  const u64 cta = blockIdx.x;\n";
+    }
+    if (!io.load && !io.prefetch) {
         o << "  {\n  u64 g0 = 0;\n";
         emit_deposit(o, "g0", "cta", opos, pa.nouter, "u64");
         emit_deposit(o, "g0", "t", tpos, tbits, "u64");
@@ -226,6 +251,7 @@ std::string gen_pass(const TilePlan<R> &tp, size_t pass) {
 
     int cur_seg = -1;
     bool first_seg = true;
+    int seg_index = 0;
     uint32_t pv[kTileMaxRegs] = {0};
     // The stored value of register v is the amplitude divided by
     //   sgn[v] * prod(rsg[v]) * 2^(-me[v] / 2):
@@ -357,6 +383,8 @@ std::string gen_pass(const TilePlan<R> &tp, size_t pass) {
             else o << "  pj = swz(jt);\n";
             const bool from_hbm = io.load && first_seg;
             first_seg = false;
+            ++seg_index;
+            const bool last_seg = seg_index == io.nseg;
             if (from_hbm) {
                 o << "  {\n";
                 emit_thread_base(sg, "gq");
@@ -374,6 +402,13 @@ std::string gen_pass(const TilePlan<R> &tp, size_t pass) {
                       << "] = a.y; }\n";
             }
             if (from_hbm) o << "  }\n";
+            if (io.prefetch && last_seg) {
+                // every thread has gathered the tile: shared memory takes the
+                // next tile's copy while this segment computes and stores
+                o << "  __syncthreads();\n  if (cta + gridDim.x < ntiles) {\n  const u64 nxt = cta + gridDim.x;\n";
+                emit_tile_copy("nxt");
+                o << "  }\n";
+            }
             continue;
         }
         // runtime condition on thread / CTA bits (branch-free select)
@@ -604,6 +639,7 @@ std::string gen_pass(const TilePlan<R> &tp, size_t pass) {
             }
             o << "  }\n";
         }
+        if (io.prefetch) o << "  }\n";  // the tile loop
         o << "}\n";
         return o.str();
     }
@@ -631,14 +667,20 @@ struct JitEntry {
 
 std::mutex g_jit_mu;
 std::unordered_map<std::string, JitEntry> g_jit;  // key: device + source
-std::unordered_map<const void *, int> g_jit_smem;   // dynamic shared memory of each compiled pass
+// per compiled pass: its dynamic shared memory, and for persistent passes the
+// CTAs per SM of the grid (0: one CTA per tile)
+struct PassLaunch {
+    int smem = 0;
+    int persistent_ctas = 0;
+};
+std::unordered_map<const void *, PassLaunch> g_jit_smem;
 
 // Shared memory a generated pass uses: the whole tile, unless direct HBM I/O
 // leaves it nothing to do (at most one segment).
 template <typename R>
 int pass_smem_bytes(const TilePlan<R> &tp, size_t pass) {
     const HbmIo io = hbm_io(tp, pass);
-    return io.load && io.store && io.nseg <= 1 ? 0 : (1 << tp.m) * int(2 * sizeof(R));
+    return io.load && io.store && io.nseg <= 1 && !io.prefetch ? 0 : (1 << tp.m) * int(2 * sizeof(R));
 }
 
 bool jit_verbose() {
@@ -932,7 +974,8 @@ sv_status jit_plan_impl(const TilePlan<R> &tp, std::vector<void *> *fns) {
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
             if (ce != cudaSuccess) return cuda_status(ce, "loading a compiled pass");
             it = g_jit.emplace(key[size_t(j)], e).first;
-            g_jit_smem[reinterpret_cast<const void *>(e.fn)] = smem;
+            g_jit_smem[reinterpret_cast<const void *>(e.fn)] =
+                PassLaunch{smem, hbm_io(tp, size_t(j)).prefetch ? tp.ctas : 0};
         }
         (*fns)[size_t(j)] = reinterpret_cast<void *>(it->second.fn);
     }
@@ -978,10 +1021,18 @@ int tile_ctas_per_sm() {
     return v >= 1 && v <= 3 ? v : 2;
 }
 
-TileConfig tile_config64(int rb, int ctas, int direct) {
+// Persistent prefetching passes (SV_TILE_PREFETCH=1; off by default, a
+// candidate of the autotuner).
+bool prefetch_enabled() {
+    const char *e = std::getenv("SV_TILE_PREFETCH");
+    return e && e[0] == '1';
+}
+
+TileConfig tile_config64(int rb, int ctas, int direct, int prefetch) {
     TileConfig c{kTileM64, rb ? rb : tile_rb64(), tile_low64(), true};
     c.ctas = ctas ? ctas : tile_ctas_per_sm();
     c.direct = direct < 0 ? direct_io_enabled() : direct != 0;
+    c.prefetch = prefetch < 0 ? prefetch_enabled() : prefetch != 0;
     return c;
 }
 
@@ -994,14 +1045,15 @@ TileConfig tile_config128() {
 
 std::string tile_config_name(const TileConfig &cfg) {
     return "m=" + std::to_string(cfg.m) + ",rb=" + std::to_string(cfg.rb) + ",low=" + std::to_string(cfg.low) +
-           ",ctas=" + std::to_string(cfg.ctas) + ",direct=" + std::to_string(int(cfg.direct));
+           ",ctas=" + std::to_string(cfg.ctas) + ",direct=" + std::to_string(int(cfg.direct)) +
+           (cfg.prefetch ? ",prefetch=1" : "");
 }
 
 std::string jit_cache_dir() { return cache_dir(); }
 
 std::string tile_codegen_key() {
     return "f32x2=" + std::to_string(int(packed_adds_enabled())) + ",ctas=" + std::to_string(tile_ctas_per_sm()) +
-           ",direct=" + std::to_string(int(direct_io_enabled()));
+           ",direct=" + std::to_string(int(direct_io_enabled())) + ",prefetch=" + std::to_string(int(prefetch_enabled()));
 }
 
 std::string tile_pass_source(const TilePlan<float> &tp, size_t i) { return gen_pass(tp, i); }
@@ -1019,15 +1071,28 @@ const char *tile_kernel_name(const sv_state *h) {
 cudaError_t launch_jit_pass(sv_state *h, void *fn, int n, int rb, uint64_t param) {
     const int M = h->dt == SV_C64 ? kTileM64 : kTileM128;
     size_t tile_bytes = (size_t(1) << M) * (h->dt == SV_C64 ? 8u : 16u);
+    int persistent = 0;
     {
         std::lock_guard<std::mutex> lock(g_jit_mu);
         auto it = g_jit_smem.find(fn);
-        if (it != g_jit_smem.end()) tile_bytes = size_t(it->second);
+        if (it != g_jit_smem.end()) {
+            tile_bytes = size_t(it->second.smem);
+            persistent = it->second.persistent_ctas;
+        }
+    }
+    unsigned long long ntiles = 1ull << (n - M);
+    unsigned grid = unsigned(ntiles);
+    if (persistent > 0) {  // persistent CTAs: the resident ones, each looping over tiles
+        int sms = 0;
+        const cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+        if (e != cudaSuccess) return e;
+        const unsigned long long resident = (unsigned long long)sms * unsigned(persistent);
+        grid = unsigned(ntiles < resident ? ntiles : resident);
     }
     void *psi = h->data;
     unsigned long long prm = param;
-    void *args[] = {&psi, &prm};
-    return cudaLaunchKernel(static_cast<const void *>(fn), dim3(1u << (n - M)), dim3(1u << (M - rb)), args, tile_bytes,
+    void *args[] = {&psi, &prm, &ntiles};
+    return cudaLaunchKernel(static_cast<const void *>(fn), dim3(grid), dim3(1u << (M - rb)), args, tile_bytes,
                             h->stream);
 }
 

@@ -543,6 +543,7 @@ sv_status plan_tiles_one(const std::vector<PGate> &G, int n, const TileConfig &c
     out->rb = cfg.rb;
     out->ctas = cfg.ctas;
     out->direct = cfg.c64 && cfg.direct;
+    out->prefetch = cfg.c64 && cfg.direct && cfg.prefetch;
     const int m = cfg.m, rb = cfg.rb, L = cfg.low;
     if (n < m) {
         set_error("tiled mode needs n >= %d", m);

@@ -170,6 +170,28 @@ def test_register_qubit_variants(S, orc, monkeypatch, rb):
     check("c64", s.to_numpy(), orc.run(c))
 
 
+@pytest.mark.parametrize("direct", ["0", "1"])
+@pytest.mark.parametrize("n,depth,seed", [(13, 8, 21), (20, 12, 22), (24, 16, 23)])
+def test_hbm_io_forms(S, orc, monkeypatch, direct, n, depth, seed):
+    """The forms of a pass's HBM access give the same states: whole tiles
+    staged through shared memory (SV_TILE_DIRECT=0), and persistent CTAs that
+    copy the next tile into shared memory while the last segment computes
+    (SV_TILE_PREFETCH=1; with 2^(n-13) tiles over the resident CTAs, from one
+    tile to many per CTA)."""
+    monkeypatch.setenv("SV_TILE_DIRECT", direct)
+    monkeypatch.setenv("SV_TILE_PREFETCH", "1")
+    c = C.random_circuit(n, depth, seed)
+    s = S.StateVector(n, "c64")
+    s.run(c, "tiled")
+    check("c64", s.to_numpy(), orc.run(c))
+    p = s.plan(c, "tiled")
+    for _ in range(3):  # direct launches, then the captured graph, then its replay
+        s.set_basis(0)
+        p.execute()
+        check("c64", s.to_numpy(), orc.run(c))
+    p.free()
+
+
 def test_plan_cache_reuse(S, orc):
     """Tiled plans are cached by circuit text (with the device, dtype, qubit
     count and planner settings in the key): running the same text again on a
