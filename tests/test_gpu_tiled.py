@@ -136,6 +136,36 @@ def test_benchmark_size_32q(S):
     torch.cuda.empty_cache()
 
 
+@pytest.mark.parametrize("mode", ["tiled", "fused"])
+def test_32q_random_amplitudes_vs_oracle(S, orc, mode):
+    """Random-circuit amplitudes at the benchmark size: the 32-qubit circuit
+    of the benchmark family (depth 12, seed 5) in complex64, 64 sampled
+    amplitudes against the oracle's exact Eq. 3 evaluation of the same
+    amplitudes (qubits 0-15 | 16-31: the 6 CZs on the edge (15, 16) are
+    decomposed, 64 branches of 16-qubit states), which the CPU tests pin to
+    the full state.  A wrong qubit in a tile slot or a lost phase shows here
+    even where a circuit and its inverse would cancel it."""
+    import torch
+
+    n = 32
+    if torch.cuda.mem_get_info()[0] < (36 << 30):
+        pytest.skip("needs 36 GiB of device memory")
+    c = C.random_circuit(n, 12, 5)
+    z = C.random_bitstrings(64, n, 3)
+    ref, cuts = orc.cut_amplitudes(c, (1 << 16) - 1, z)
+    assert cuts == 6
+    s = S.StateVector(n, "c64")
+    s.run(c, mode)
+    got = s.amplitudes(z)
+    rms = float(np.sqrt(np.mean(np.abs(ref) ** 2)))
+    err = float(np.max(np.abs(got - ref)))
+    assert err <= TOL_C64_AMP  # the complex64 bound (norm 1)
+    assert err <= 2e-5 * rms, (err, rms)  # and a relative one at this amplitude size
+    s.free()
+    del s
+    torch.cuda.empty_cache()
+
+
 def test_30q_c128_roundtrip(S):
     n = 30
     s = S.StateVector(n, "c128")
