@@ -960,6 +960,40 @@ def bench_ghz128(S, C):
             "note": "end to end: host bit strings (2 GiB) in, 2^27 complex128 out"}
 
 
+def summarize(line: dict) -> dict:
+    """Headline figures of the comparisons and extras, a few hundred bytes."""
+    def g(d, *path):
+        for k in path:
+            if not isinstance(d, dict) or k not in d:
+                return None
+            d = d[k]
+        return round(d, 4) if isinstance(d, float) else d
+
+    out = {"tiled_gates_per_s": g(line, "value"), "ms_per_step": g(line, "ms_per_step"),
+           "fp32_frac": g(line, "roofline", "frac"), "hbm_frac": g(line, "roofline", "hbm", "frac"),
+           "per_pass_floor_ms": g(line, "roofline", "floors_ms", "per_pass_max_sum"),
+           "autotune_chosen": g(line, "config", "autotune", "chosen"),
+           "fused_gates_per_s": g(line, "compare", "fused", "gates_per_s"),
+           "pergate_gates_per_s": g(line, "compare", "pergate", "gates_per_s"),
+           "pergate_hbm_frac": g(line, "compare", "pergate", "roofline", "frac")}
+    ex = line.get("extras") or {}
+    out["enc2b_35q"] = {"s_per_circuit": g(ex, "enc2b_35q", "s_per_circuit"),
+                        "gates_per_s": g(ex, "enc2b_35q", "gates_per_s"),
+                        "one_minus_fidelity_24q": g(ex, "enc2b_35q", "fidelity_24q", "one_minus_fidelity")}
+    out["cut_48q_ms"] = g(ex, "cut_48q", "ms_per_call")
+    out["qft_32q_gates_per_s"] = g(ex, "qft_32q", "tiled", "gates_per_s")
+    out["h_sweep_min_frac"] = g(ex, "h_sweep_32q", "min_frac")
+    out["random_30q_gates_per_s"] = {"c64": g(ex, "random_30q", "c64", "gates_per_s"),
+                                     "c128": g(ex, "random_30q", "c128", "gates_per_s")}
+    out["expect_32q_ms"] = g(ex, "expect_32q", "ms_per_call")
+    out["batch_64_speedup"] = g(ex, "batch_64", "speedup")
+    depths = (g(ex, "cut_42q_depth", "by_depth") or {})
+    out["cut_42q_s_by_depth"] = {str(k): (round(v["s_per_call"], 3) if "s_per_call" in v else "skipped")
+                                 for k, v in depths.items()}
+    out["ghz128_s"] = g(ex, "ghz128_m2e27", "s_per_call")
+    return out
+
+
 def run_ours(args, world, rank, local):
     import numpy as np
     import torch
@@ -1136,6 +1170,9 @@ def run_ours(args, world, rank, local):
             "compare": compare, "extras": extras, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": args.steps * (launches_per_step + 1),
         }
+        # a compact digest of the comparisons and extras last, so that a reader
+        # of only the line's end still sees them
+        line["summary"] = summarize(line)
         print(json.dumps(line), flush=True)
 
 

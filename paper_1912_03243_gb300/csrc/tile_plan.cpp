@@ -444,41 +444,55 @@ int segments_first_fit(const std::vector<PGate> &G, std::vector<int> pending, in
 // growth by applicable-gate count started from each of the `width` best
 // single qubits; each candidate is rolled out with first fit and the one
 // needing the fewest segments wins (ties: first fit, then more gates now).
+// avoid: qubits a register set should leave to the lanes when that costs no
+// segment (the low tile bits of a segment that loads straight from HBM); the
+// greedy growths are then also tried without them.
 uint64_t rset_lookahead(const std::vector<PGate> &G, const std::vector<int> &pending, uint64_t T, int rb, uint64_t all,
-                        int width) {
+                        int width, uint64_t avoid = 0) {
     std::vector<uint64_t> cand{rset_first_fit(G, pending, rb)};
-    std::vector<std::pair<int, int>> first;
-    for (int q = 0; q < 64; ++q)
-        if (T >> q & 1) first.push_back({count_applicable(G, pending, uint64_t(1) << q, all), q});
-    std::sort(first.begin(), first.end(),
-              [](auto a, auto b) { return a.first > b.first || (a.first == b.first && a.second < b.second); });
-    for (int i = 0; i < width && i < int(first.size()); ++i) {
-        uint64_t R = uint64_t(1) << first[size_t(i)].second;
-        while (popc(R) < rb && popc(R) < popc(T)) {
-            int best_q = -1, best_c = -1;
-            for (int q = 0; q < 64; ++q) {
-                if (!(T >> q & 1) || (R >> q & 1)) continue;
-                const int c = count_applicable(G, pending, R | (uint64_t(1) << q), all);
-                if (c > best_c) {
-                    best_c = c;
-                    best_q = q;
+    auto grow = [&](uint64_t TT) {
+        std::vector<std::pair<int, int>> first;
+        for (int q = 0; q < 64; ++q)
+            if (TT >> q & 1) first.push_back({count_applicable(G, pending, uint64_t(1) << q, all), q});
+        std::sort(first.begin(), first.end(),
+                  [](auto a, auto b) { return a.first > b.first || (a.first == b.first && a.second < b.second); });
+        for (int i = 0; i < width && i < int(first.size()); ++i) {
+            uint64_t R = uint64_t(1) << first[size_t(i)].second;
+            while (popc(R) < rb && popc(R) < popc(TT)) {
+                int best_q = -1, best_c = -1;
+                for (int q = 0; q < 64; ++q) {
+                    if (!(TT >> q & 1) || (R >> q & 1)) continue;
+                    const int c = count_applicable(G, pending, R | (uint64_t(1) << q), all);
+                    if (c > best_c) {
+                        best_c = c;
+                        best_q = q;
+                    }
                 }
+                R |= uint64_t(1) << best_q;
             }
-            R |= uint64_t(1) << best_q;
+            if (std::find(cand.begin(), cand.end(), R) == cand.end()) cand.push_back(R);
         }
-        if (std::find(cand.begin(), cand.end(), R) == cand.end()) cand.push_back(R);
-    }
+    };
+    grow(T);
+    const size_t ngrow = cand.size();
+    if (avoid && popc(T & ~avoid) >= rb) grow(T & ~avoid);
     uint64_t best = cand[0];
     int best_ns = 1 << 30, best_cnt = -1;
-    for (uint64_t R : cand) {
+    bool best_clear = false;
+    for (size_t i = 0; i < cand.size(); ++i) {
+        const uint64_t R = cand[i];
         std::vector<int> rest = pending;
         take_pass(G, rest, R, all);
         const int ns = 1 + segments_first_fit(G, rest, rb, all);
         const int cnt = int(pending.size() - rest.size());
-        if (ns < best_ns || (ns == best_ns && R != cand[0] && best != cand[0] && cnt > best_cnt)) {
+        const bool clear = avoid && !(R & avoid);
+        if (i >= ngrow && !(ns < best_ns || (ns == best_ns && clear && !best_clear))) continue;
+        if (ns < best_ns || (ns == best_ns && clear && !best_clear) ||
+            (ns == best_ns && clear == best_clear && R != cand[0] && best != cand[0] && cnt > best_cnt)) {
             best_ns = ns;
             best_cnt = cnt;
             best = R;
+            best_clear = clear;
         }
     }
     return best;
@@ -644,7 +658,12 @@ sv_status plan_tiles_one(const std::vector<PGate> &G, int n, const TileConfig &c
         };
         while (!remaining.empty()) {
             const int sw = seg_lookahead_width();
-            uint64_t Rset = sw > 0 ? rset_lookahead(G, remaining, T, rb, all, sw) : rset_first_fit(G, remaining, rb);
+            // the first segment loads straight from HBM when tile bits 0-2 are lanes
+            const uint64_t low3 = (cfg.c64 && cfg.direct && remaining.size() == pass_ops.size() && L >= 3)
+                                      ? ((uint64_t(1) << pa.tile_pos[0]) | (uint64_t(1) << pa.tile_pos[1]) |
+                                         (uint64_t(1) << pa.tile_pos[2]))
+                                      : 0;
+            uint64_t Rset = sw > 0 ? rset_lookahead(G, remaining, T, rb, all, sw, low3) : rset_first_fit(G, remaining, rb);
             for (int k = m - 1; k >= 0 && popc(Rset) < rb; --k) {
                 // fill with the highest tile bits (keeps the low, contiguous
                 // ones free for lanes: coalesced HBM access)
