@@ -186,7 +186,8 @@ sv_status sv_plan_execute_timed(sv_plan p, void *const *events, int64_t n_events
 /* The autotuner's record of an SV_MODE_AUTO plan as JSON text: each
  * candidate strategy with its measured ms per execution and the chosen one
  * ({"timed": false, ...} when the choice was remembered from an earlier
- * tuning or no scratch state fitted); "" for other modes.  buf (cap bytes,
+ * tuning, there was one candidate only, or no scratch state fitted); "" for
+ * other modes.  buf (cap bytes,
  * NUL-terminated, may be NULL), *len = the full length. */
 sv_status sv_plan_tuning(sv_plan p, char *buf, size_t cap, size_t *len);
 sv_status sv_plan_free(sv_plan p);

@@ -412,6 +412,12 @@ sv_status create_auto_plan(sv_state *h, const char *text, const Circuit &c, sv_p
             if (!s) (*out)->tuning = "{\"timed\": false, \"remembered\": true, \"chosen\": \"" + known + "\"}";
             return s;
         }
+    if (cand.size() == 1) {  // nothing to choose between (the two-byte code)
+        sv_status s = create_plan(h, text, c, cand[0], out);
+        if (!s)
+            (*out)->tuning = "{\"timed\": false, \"reason\": \"one candidate\", \"chosen\": \"" + cand[0].name() + "\"}";
+        return s;
+    }
     size_t best = 0;
     std::string report;
     sv_status s = time_candidates(h, text, c, cand, &best, &report);
