@@ -181,7 +181,7 @@ TileConfig default_config(const sv_state *h) { return h->dt == SV_C64 ? tile_con
 // Build the plan of one strategy for the handle (text already parsed into c).
 sv_status create_plan(sv_state *h, const char *text, const Circuit &c, const Strategy &st, sv_plan_s **out) {
     *out = nullptr;
-    const int tile_m = h->dt == SV_C64 ? kTileM64 : kTileM128;
+    const int tile_m = st.mode == SV_MODE_TILED ? st.cfg.m : (h->dt == SV_C64 ? kTileM64 : kTileM128);
     const bool tiled = st.mode == SV_MODE_TILED && h->n >= tile_m;
     std::string key;
     if (tiled && text) {
@@ -260,10 +260,13 @@ std::vector<Strategy> candidates(const sv_state *h) {
     }
     if (h->n >= tile_m) {
         if (h->dt == SV_C64) {
-            // the generator's register bits, CTAs per SM and HBM I/O forms
-            const int opts[][4] = {{5, 2, 1, 0}, {5, 2, 1, 1}, {5, 2, 0, 0}, {4, 2, 1, 0}, {5, 3, 1, 0}};
+            // the generator's configurations: register bits, CTAs per SM,
+            // direct HBM I/O, prefetching, tile bits
+            const int opts[][5] = {{5, 2, 1, 0, 13}, {5, 2, 1, 1, 13}, {5, 2, 0, 0, 13},
+                                   {4, 2, 1, 0, 13}, {5, 3, 1, 0, 13}, {5, 4, 1, 0, 12}};
             for (const auto &o : opts)
-                v.push_back(Strategy{SV_MODE_TILED, tile_config64(o[0], o[1], o[2], o[3]), 0});
+                if (h->n >= o[4])
+                    v.push_back(Strategy{SV_MODE_TILED, tile_config64(o[0], o[1], o[2], o[3], o[4]), 0});
         } else {
             v.push_back(Strategy{SV_MODE_TILED, tile_config128(), 0});
         }

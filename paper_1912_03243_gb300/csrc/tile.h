@@ -161,7 +161,9 @@ int tile_ctas_per_sm();
 // The tile configuration of complex64 / complex128 passes: the environment's
 // defaults, or the given register bits, CTAs per SM and direct I/O (an
 // autotuner's candidate; 0 / -1 keep the default).
-TileConfig tile_config64(int rb = 0, int ctas = 0, int direct = -1, int prefetch = -1);
+TileConfig tile_config64(int rb = 0, int ctas = 0, int direct = -1, int prefetch = -1, int m = 0);
+// Tile bits of complex64 passes (SV_TILE_M overrides: 12 or 13).
+int tile_m64();
 TileConfig tile_config128();
 // Folder of the compiled-pass disk cache ("" when there is none).
 std::string jit_cache_dir();

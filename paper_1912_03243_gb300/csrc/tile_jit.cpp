@@ -672,6 +672,7 @@ std::unordered_map<std::string, JitEntry> g_jit;  // key: device + source
 struct PassLaunch {
     int smem = 0;
     int persistent_ctas = 0;
+    int m = 0;  // tile bits
 };
 std::unordered_map<const void *, PassLaunch> g_jit_smem;
 
@@ -975,7 +976,7 @@ sv_status jit_plan_impl(const TilePlan<R> &tp, std::vector<void *> *fns) {
             if (ce != cudaSuccess) return cuda_status(ce, "loading a compiled pass");
             it = g_jit.emplace(key[size_t(j)], e).first;
             g_jit_smem[reinterpret_cast<const void *>(e.fn)] =
-                PassLaunch{smem, hbm_io(tp, size_t(j)).prefetch ? tp.ctas : 0};
+                PassLaunch{smem, hbm_io(tp, size_t(j)).prefetch ? tp.ctas : 0, tp.m};
         }
         (*fns)[size_t(j)] = reinterpret_cast<void *>(it->second.fn);
     }
@@ -1014,11 +1015,12 @@ bool direct_io_enabled() {
 }
 
 // CTAs per SM the pass kernels are compiled for (register budget); the
-// shared tile (64 KiB) allows up to 3.  SV_TILE_CTAS overrides.
+// shared tile (64 KiB) allows up to 3, a 2^12 tile (32 KiB) 4 and more.
+// SV_TILE_CTAS overrides (1 to 4).
 int tile_ctas_per_sm() {
     const char *e = std::getenv("SV_TILE_CTAS");
     const int v = e ? std::atoi(e) : 2;
-    return v >= 1 && v <= 3 ? v : 2;
+    return v >= 1 && v <= 4 ? v : 2;
 }
 
 // Persistent prefetching passes (SV_TILE_PREFETCH=1; off by default, a
@@ -1028,8 +1030,15 @@ bool prefetch_enabled() {
     return e && e[0] == '1';
 }
 
-TileConfig tile_config64(int rb, int ctas, int direct, int prefetch) {
-    TileConfig c{kTileM64, rb ? rb : tile_rb64(), tile_low64(), true};
+// Tile bits of complex64 passes (SV_TILE_M overrides, 12 or 13).
+int tile_m64() {
+    const char *e = std::getenv("SV_TILE_M");
+    const int v = e ? std::atoi(e) : kTileM64;
+    return v == 12 || v == 13 ? v : kTileM64;
+}
+
+TileConfig tile_config64(int rb, int ctas, int direct, int prefetch, int m) {
+    TileConfig c{m ? m : tile_m64(), rb ? rb : tile_rb64(), tile_low64(), true};
     c.ctas = ctas ? ctas : tile_ctas_per_sm();
     c.direct = direct < 0 ? direct_io_enabled() : direct != 0;
     c.prefetch = prefetch < 0 ? prefetch_enabled() : prefetch != 0;
@@ -1069,7 +1078,7 @@ const char *tile_kernel_name(const sv_state *h) {
 }
 
 cudaError_t launch_jit_pass(sv_state *h, void *fn, int n, int rb, uint64_t param) {
-    const int M = h->dt == SV_C64 ? kTileM64 : kTileM128;
+    int M = h->dt == SV_C64 ? kTileM64 : kTileM128;
     size_t tile_bytes = (size_t(1) << M) * (h->dt == SV_C64 ? 8u : 16u);
     int persistent = 0;
     {
@@ -1078,6 +1087,7 @@ cudaError_t launch_jit_pass(sv_state *h, void *fn, int n, int rb, uint64_t param
         if (it != g_jit_smem.end()) {
             tile_bytes = size_t(it->second.smem);
             persistent = it->second.persistent_ctas;
+            M = it->second.m;
         }
     }
     unsigned long long ntiles = 1ull << (n - M);

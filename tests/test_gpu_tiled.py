@@ -188,6 +188,19 @@ def test_register_budget_variants(S, orc, monkeypatch, ctas):
     check("c64", s.to_numpy(), orc.run(c))
 
 
+@pytest.mark.parametrize("n", [12, 13, 21])
+def test_twelve_bit_tiles(S, orc, monkeypatch, n):
+    """Passes on 2^12-amplitude tiles (SV_TILE_M=12: 128-thread CTAs, four
+    per SM) give the same states as the default 2^13 tiles, from one tile
+    upwards."""
+    monkeypatch.setenv("SV_TILE_M", "12")
+    monkeypatch.setenv("SV_TILE_CTAS", "4")
+    c = C.random_circuit(n, 10, 17)
+    s = S.StateVector(n, "c64")
+    s.run(c, "tiled")
+    check("c64", s.to_numpy(), orc.run(c))
+
+
 @pytest.mark.parametrize("rb", ["4", "6"])
 def test_register_qubit_variants(S, orc, monkeypatch, rb):
     """Passes generated for 4 or 6 register qubits per thread (SV_TILE_RB:
