@@ -160,7 +160,10 @@ def test_32q_random_amplitudes_vs_oracle(S, orc, mode):
     rms = float(np.sqrt(np.mean(np.abs(ref) ** 2)))
     err = float(np.max(np.abs(got - ref)))
     assert err <= TOL_C64_AMP  # the complex64 bound (norm 1)
-    assert err <= 2e-5 * rms, (err, rms)  # and a relative one at this amplitude size
+    # and a relative one at this amplitude size: FP32 butterflies (tiled), or
+    # split-BF16 products of about 2^-16 relative error each, over some 30
+    # dense blocks (fused)
+    assert err <= (2e-5 if mode == "tiled" else 2e-4) * rms, (err, rms)
     s.free()
     del s
     torch.cuda.empty_cache()
