@@ -37,6 +37,14 @@ struct EncGateArgs {
     float u[8];
 };
 
+}  // namespace
+}  // namespace sv
+
+#include "enc_run.h"
+
+namespace sv {
+namespace {
+
 __device__ __forceinline__ uint64_t insert_zero(uint64_t x, int p) {
     const uint64_t lo = x & ((uint64_t(1) << p) - 1);
     return ((x ^ lo) << 1) | lo;
@@ -500,6 +508,95 @@ __global__ void __launch_bounds__(256) k_enc_xblocks(uint4 *__restrict__ codes, 
     }
 }
 
+// ---------------------------------------------------------------- runs of in-block gates
+// A run of consecutive gates that each act inside blocks (2x2 updates with a
+// target below bit 8, any control) or are sign flips (+-1 diagonals on any
+// qubits) is applied in one pass: each warp holds one block's codes and
+// scale in registers and goes through the run in circuit order.  A gate is
+// the same decode -> FP32 update -> block maximum -> encode as in
+// k_enc_gate_in (the same functions, in the same order), and a flip negates
+// codes as k_enc_flip does, so every block's codes and scale after the run
+// are those of the gates applied one pass at a time: bit-exact.  A gate whose
+// block-level control is 0 leaves the block as it is (decoding and
+// re-encoding with an unchanged scale is the identity).
+
+template <int SHAPE>
+__device__ __forceinline__ void run_gate_in(const EncRunOp &op, int lane, Lane8 &x) {
+    EncGateArgs a{};
+    a.t = op.t;
+    a.c = op.c;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a.u[k] = op.u[k];
+    if (op.t < 3) {
+        if (op.t == 0)
+            lane_pairs<SHAPE, 1>(a, lane, x);
+        else if (op.t == 1)
+            lane_pairs<SHAPE, 2>(a, lane, x);
+        else
+            lane_pairs<SHAPE, 4>(a, lane, x);
+    } else {
+        const int lb = 1 << (op.t - 3);
+        const bool upper = lane & lb;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const float pr = __shfl_xor_sync(0xffffffffu, x.re[j], lb);
+            const float pi = __shfl_xor_sync(0xffffffffu, x.im[j], lb);
+            if (!ctl_ok(a.c, lane, j)) continue;
+            float ar = upper ? pr : x.re[j], ai = upper ? pi : x.im[j];
+            float br = upper ? x.re[j] : pr, bi = upper ? x.im[j] : pi;
+            gate_pair_s<SHAPE>(a.u, ar, ai, br, bi);
+            x.re[j] = upper ? br : ar;
+            x.im[j] = upper ? bi : ai;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(32 * kWarpsPerCta) k_enc_run_in(int4 *__restrict__ codes, float *__restrict__ scales,
+                                                                  uint64_t nblocks, const EncRunOp *__restrict__ gops,
+                                                                  int nops) {
+    __shared__ float tab[kTabFloats];
+    __shared__ EncRunOp ops[kEncRunMaxOps];
+    for (int i = threadIdx.x; i < nops; i += blockDim.x) ops[i] = gops[i];
+    load_table(tab);  // (its barrier also publishes the ops)
+    const int lane = threadIdx.x & 31;
+    const uint64_t wid = uint64_t(blockIdx.x) * kWarpsPerCta + (threadIdx.x >> 5);
+    const uint64_t nw = uint64_t(gridDim.x) * kWarpsPerCta;
+    for (uint64_t b = wid; b < nblocks; b += nw) {
+        int4 raw = codes[b * 32 + lane];
+        float s = scales[b];
+        for (int i = 0; i < nops; ++i) {
+            const EncRunOp &op = ops[i];
+            if ((b & op.hi_mask) != op.hi_val) continue;  // block-level condition not met
+            if (op.kind == 1) {  // sign flip of the codes whose in-block bits match
+                uint32_t *x = reinterpret_cast<uint32_t *>(&raw);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    uint32_t bm = 0;
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const uint32_t idx = uint32_t(lane) * 8 + 2 * k + h;
+                        if ((idx & op.lo_mask) == op.lo_val) bm |= 0xFFFFu << (16 * h);
+                    }
+                    x[k] = (x[k] & ~bm) | (__vneg4(x[k]) & bm);
+                }
+                continue;
+            }
+            Lane8 x;
+            decode_lane(raw, s, tab, lane, x);
+            switch (op.shape) {
+                case ENC_REAL: run_gate_in<ENC_REAL>(op, lane, x); break;
+                case ENC_DIAG: run_gate_in<ENC_DIAG>(op, lane, x); break;
+                case ENC_DIAG1: run_gate_in<ENC_DIAG1>(op, lane, x); break;
+                default: run_gate_in<ENC_GENERAL>(op, lane, x); break;
+            }
+            s = warp_max(lane_absmax(x));
+            raw = encode_lane(x, s);
+        }
+        codes[b * 32 + lane] = raw;
+        if (lane == 0) scales[b] = s;
+    }
+}
+
 int enc_grid(uint64_t nwork) {
     uint64_t b = (nwork + kWarpsPerCta - 1) / kWarpsPerCta;
     const uint64_t cap = 152ull * 16;
@@ -596,6 +693,57 @@ cudaError_t launch_enc_gate1(sv_state *h, const Gate1 &g) {
             default: k_enc_gate_across<ENC_GENERAL><<<grid, block, 0, h->stream>>>(codes, h->scales, a); break;
         }
     }
+    return cudaGetLastError();
+}
+
+// The matrix shape of a gate from exact zeros of its FP32 entries.
+static int enc_shape(const float *u) {
+    const bool real = u[1] == 0.0f && u[3] == 0.0f && u[5] == 0.0f && u[7] == 0.0f;
+    const bool diag = u[2] == 0.0f && u[3] == 0.0f && u[4] == 0.0f && u[5] == 0.0f;
+    const bool one = diag && u[0] == 1.0f && u[1] == 0.0f;
+    return one ? ENC_DIAG1 : diag ? ENC_DIAG : real ? ENC_REAL : ENC_GENERAL;
+}
+
+bool enc_run_op(int n, const Gate1 &g, EncRunOp *op) {
+    if (n < kEncBlockLog2) return false;
+    *op = EncRunOp{};
+    const Cplx *u = g.u;
+    auto is = [](const Cplx &z, double re) { return z.re == re && z.im == 0.0; };
+    if (is(u[1], 0) && is(u[2], 0) && (is(u[0], 1) || is(u[0], -1)) && (is(u[3], 1) || is(u[3], -1))) {
+        // +-1 diagonal: a sign flip on any qubits (identity: an empty flip)
+        uint64_t m = g.control >= 0 ? (uint64_t(1) << g.control) : 0, v = m;
+        if (!(is(u[0], -1) && is(u[3], -1))) {
+            m |= uint64_t(1) << g.target;
+            if (is(u[3], -1)) v |= uint64_t(1) << g.target;
+        }
+        op->kind = 1;
+        op->lo_mask = uint32_t(m & 0xFFu);
+        op->lo_val = uint32_t(v & 0xFFu);
+        op->hi_mask = m >> kEncBlockLog2;
+        op->hi_val = v >> kEncBlockLog2;
+        if (is(u[0], 1) && is(u[3], 1)) {  // identity: a flip that matches no amplitude
+            op->lo_mask = 0;
+            op->lo_val = 1;
+        }
+        return true;
+    }
+    if (g.target >= kEncBlockLog2) return false;
+    op->kind = 0;
+    op->t = g.target;
+    op->c = g.control >= 0 && g.control < kEncBlockLog2 ? g.control : -1;
+    if (g.control >= kEncBlockLog2) op->hi_mask = op->hi_val = uint64_t(1) << (g.control - kEncBlockLog2);
+    for (int k = 0; k < 4; ++k) {
+        op->u[2 * k] = float(g.u[k].re);
+        op->u[2 * k + 1] = float(g.u[k].im);
+    }
+    op->shape = enc_shape(op->u);
+    return true;
+}
+
+cudaError_t launch_enc_run(sv_state *h, const EncRunOp *d_ops, int nops) {
+    const uint64_t nb = uint64_t(1) << (h->n - kEncBlockLog2);
+    k_enc_run_in<<<enc_grid(nb), 32 * kWarpsPerCta, 0, h->stream>>>(static_cast<int4 *>(h->data), h->scales, nb,
+                                                                    d_ops, nops);
     return cudaGetLastError();
 }
 

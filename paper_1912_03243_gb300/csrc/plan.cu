@@ -44,6 +44,7 @@ void destroy_plan(sv_plan_s *p) {
         if (e) cudaEventDestroy(e);
     if (p->gstream) cudaStreamDestroy(p->gstream);
     if (p->d_tcA) cudaFree(p->d_tcA);
+    if (p->d_encops) cudaFree(p->d_encops);
     delete p;
 }
 
@@ -78,6 +79,57 @@ sv_status build_fused_plan(sv_state *h, const Circuit &c, sv_plan_s *p, int kfix
         for (size_t i = 0; i < p->blocks.size(); ++i) p->launches.push_back(PlanLaunch{3, int(i), pass_bytes});
     }
     p->bytes = pass_bytes * double(p->launches.size());
+    return SV_OK;
+}
+
+// Two-byte code: runs of consecutive in-block gates and sign flips become one
+// pass each (k_enc_run_in) where the run's gates, one pass each, would move
+// more bytes than one pass over the code; the other gates keep their own
+// passes.  SV_ENC_RUNS=0 keeps one pass per gate.
+bool enc_runs_enabled() {
+    const char *e = std::getenv("SV_ENC_RUNS");
+    return !(e && e[0] == '0');
+}
+
+sv_status build_enc_runs(sv_state *h, sv_plan_s *p) {
+    if (h->n < kEncBlockLog2 || !enc_runs_enabled()) return SV_OK;
+    const double amps = double(uint64_t(1) << h->n);
+    const double pass_bytes = 2.0 * amps * 2.0 + 2.0 * (amps / kEncBlock) * 4.0;
+    std::vector<EncRunOp> ops;
+    const size_t ng = p->pergate.size();
+    size_t i = 0;
+    while (i < ng) {
+        EncRunOp op;
+        size_t j = i;
+        double alone = 0.0;
+        while (j < ng && j - i < size_t(kEncRunMaxOps) && enc_run_op(h->n, p->pergate[j], &op)) {
+            alone += gate1_bytes(h, p->pergate[j]);
+            ++j;
+        }
+        if (j - i >= 2 && alone > pass_bytes) {
+            PlanLaunch l{4, int(p->encruns.size()), pass_bytes};
+            p->encruns.push_back({int(ops.size()), int(j - i), int(j - i)});
+            for (size_t k = i; k < j; ++k) {
+                enc_run_op(h->n, p->pergate[k], &op);
+                ops.push_back(op);
+            }
+            p->launches.push_back(l);
+            p->bytes += pass_bytes;
+            i = j;
+            continue;
+        }
+        const size_t stop = j > i ? j : i + 1;  // the gates of a short run, or one other gate
+        for (size_t k = i; k < stop; ++k) {
+            const double b = gate1_bytes(h, p->pergate[k]);
+            p->launches.push_back(PlanLaunch{0, int(k), b});
+            p->bytes += b;
+        }
+        i = stop;
+    }
+    if (!ops.empty()) {
+        SV_CUDA_TRY(cudaMalloc(&p->d_encops, ops.size() * sizeof(EncRunOp)));
+        SV_CUDA_TRY(cudaMemcpy(p->d_encops, ops.data(), ops.size() * sizeof(EncRunOp), cudaMemcpyHostToDevice));
+    }
     return SV_OK;
 }
 
@@ -119,6 +171,10 @@ cudaError_t launch_one(sv_plan_s *p, const PlanLaunch &l) {
         const FusedBlock &b = p->blocks[size_t(l.index)];
         return launch_fused(p->h, b.k, b.qubits, b.U.data());
     }
+    if (l.kind == 4) {
+        const sv_plan_s::EncRun &r = p->encruns[size_t(l.index)];
+        return launch_enc_run(p->h, p->d_encops + r.first, r.count);
+    }
     return launch_jit_pass(p->h, p->tfns[size_t(l.index)], p->h->n, p->tile_rb);
 }
 
@@ -128,6 +184,7 @@ const char *launch_name(const sv_plan_s *p, const PlanLaunch &l) {
                                      "k_fused_tc<k=4>", "k_fused_tc<k=5>", "k_fused_tc<k=6>"};
     if (l.kind == 2) return tc_names[p->tcargs[size_t(l.index)].k];
     if (l.kind == 3) return p->h->dt == SV_C64 ? "k_fused_dense<f32>" : "k_fused_dense<f64>";
+    if (l.kind == 4) return "k_enc_run_in";
     return tile_kernel_name(p->h);
 }
 
@@ -219,11 +276,13 @@ sv_status create_plan(sv_state *h, const char *text, const Circuit &c, const Str
     } else if (st.mode == SV_MODE_PERGATE || h->n < tile_m) {
         // per-gate updates (also the tiled mode's path for states smaller than one tile)
         p->pergate = lower_to_gate1(c);
-        for (size_t i = 0; i < p->pergate.size(); ++i) {
-            const double b = gate1_bytes(h, p->pergate[i]);
-            p->launches.push_back(PlanLaunch{0, int(i), b});
-            p->bytes += b;
-        }
+        s = h->dt == SV_ENC2B ? build_enc_runs(h, p) : SV_OK;
+        if (!s && p->launches.empty())
+            for (size_t i = 0; i < p->pergate.size(); ++i) {
+                const double b = gate1_bytes(h, p->pergate[i]);
+                p->launches.push_back(PlanLaunch{0, int(i), b});
+                p->bytes += b;
+            }
     } else {
         s = build_tile_plan(h, c, p, st.cfg);
         if (!s && !key.empty()) {

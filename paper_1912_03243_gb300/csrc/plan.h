@@ -4,6 +4,7 @@
 #include <string>
 #include <vector>
 
+#include "enc_run.h"
 #include "fused_tc.h"
 #include "sv_internal.h"
 #include "tile.h"
@@ -45,7 +46,8 @@ const char *gate1_kernel_name(const sv_state *h, const Gate1 &g);
 // One kernel launch of a plan.
 struct PlanLaunch {
     int kind;      // 0: per-gate update pergate[index]; 1: compiled tile pass tfns[index];
-                   // 2: tensor-core block tcargs[index]; 3: CUDA-core block blocks[index]
+                   // 2: tensor-core block tcargs[index]; 3: CUDA-core block blocks[index];
+                   // 4: run of in-block two-byte-code gates encruns[index]
     int index;
     double bytes;  // algorithmic bytes
     double lane_ops = 0.0;  // compiled tile passes: FP32 lane operations per amplitude (at least)
@@ -57,6 +59,11 @@ struct sv_plan_s {
     int mode = 0;
     int64_t gates = 0;                     // gates of the circuit text
     std::vector<sv::Gate1> pergate;        // per-gate updates
+    struct EncRun {
+        int first, count, gates;           // ops d_encops[first .. first + count), circuit gates they apply
+    };
+    std::vector<EncRun> encruns;           // two-byte code: runs of in-block gates, one pass each
+    sv::EncRunOp *d_encops = nullptr;      // their ops (device)
     std::vector<void *> tfns;              // compiled tile passes
     int tile_rb = 0;                       // their register bits per thread
     std::vector<double> tile_lane_ops;     // their FP32 lane operations per amplitude

@@ -131,3 +131,41 @@ def test_fidelity_24q(S, orc, record_property):
     record_property("fidelity_enc2b_24q_d12", f)
     print(f"enc2b fidelity 24q d12: {f:.6f}")
     assert f > 0.95
+
+
+@pytest.mark.parametrize("n,seed", [(9, 1), (12, 2), (14, 3)])
+def test_in_block_runs_bit_exact(S, orc, n, seed):
+    """Runs of consecutive in-block gates and sign flips applied in one pass
+    each (the default per-gate plan of the two-byte code) give the CPU codec
+    mirror's codes: every gate kind of the format on random qubits, so runs
+    hold controls inside and outside the blocks, X, P, U and CZ/CP flips, and
+    runs are broken by gates across blocks."""
+    c = C.random_unitary_gates(n, 400, 50 + seed)
+    layer_like = C.random_circuit(n, 8, seed)  # long runs: in-block layers and CZ rows
+    for circ in (c, layer_like):
+        rc, rs = orc.enc_run(circ)
+        enc = S.StateVector(n, "enc2b")
+        plan = enc.plan(circ, "pergate")
+        kinds = {name for name, _ in plan.launch_info()}
+        plan.execute()
+        gc, gs = enc.codes()
+        assert np.array_equal(gc, rc), n
+        assert np.array_equal(gs.view(np.uint32), rs.view(np.uint32)), n
+        plan.free()
+    assert "k_enc_run_in" in kinds
+
+
+def test_in_block_runs_equal_one_pass_per_gate(S, monkeypatch):
+    """At 22 qubits (beyond the mirror's quick range) the fused runs and one
+    pass per gate (SV_ENC_RUNS=0) write the same codes and scales."""
+    n = 22
+    c = C.random_circuit(n, 6, 8)
+    out = []
+    for runs in ("1", "0"):
+        monkeypatch.setenv("SV_ENC_RUNS", runs)
+        enc = S.StateVector(n, "enc2b")
+        enc.run(c, "pergate")
+        out.append(enc.codes())
+        enc.free()
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1].view(np.uint32), out[1][1].view(np.uint32))
