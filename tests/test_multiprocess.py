@@ -86,8 +86,9 @@ def test_bench_max_over_ranks_gloo(tmp_path):
 
 
 def test_bench_reference_arm_two_ranks():
-    """The driver's launch form for N > 1: rank 0 prints one JSON line, the
-    other rank exits 0 without work."""
+    """The benchmark's launch form for N > 1 (torch.distributed.run, two
+    ranks): rank 0 prints one JSON line, the other rank exits 0 without
+    work."""
     cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node=2",
            "--master-addr=127.0.0.1", f"--master-port={free_port()}", "bench.py", "--impl", "reference",
            "--gpus", "2", "--steps", "1", "--warmup", "0", "--qubits", "16"]
