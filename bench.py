@@ -258,16 +258,18 @@ def oracle_point(n, depth, seed, budget_s: float, min_s: float):
     return done / t_used, done, t_used
 
 
-def oracle_sample(args, budget_s: float, min_s: float = 10.0, ns=None):
+def oracle_sample(args, budget_s: float, min_s: float = 10.0, ns=None, weights=None):
     """Time the CPU oracle at one or more qubit counts below args.n and scale
     each to args.n by 2^(n_sample - n) (its cost per gate is proportional to
     the amplitude count; the spread of the scaled values checks that).  The
     value is the point at the largest n.  Returns (gates/s at args.n,
     description, seconds, points)."""
     ns = ns or [min(args.n, 26)]
+    weights = weights or [1.0] * len(ns)
+    wsum = sum(weights)
     points = []
-    for n in ns:
-        gps, done, t = oracle_point(n, args.depth, args.seed, budget_s / len(ns), min_s / len(ns))
+    for n, w in zip(ns, weights):
+        gps, done, t = oracle_point(n, args.depth, args.seed, budget_s * w / wsum, min_s * w / wsum)
         points.append({"n": n, "gates": done, "s": round(t, 3), "gates_per_s": gps,
                        "scaled_to_n": gps * 2.0 ** (n - args.n)})
     top = points[-1]
@@ -1143,8 +1145,11 @@ def run_ours(args, world, rank, local):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        ns = [m for m in (20, 24, 26, 28) if m <= args.n]
-        v, sdesc, tcpu, pts = oracle_sample(args, budget_s=40.0, min_s=24.0, ns=ns)
+        # most of the time on the largest point (26 qubits, a 1 GiB state, well
+        # beyond the host caches), the smaller ones to check the 2^n scaling
+        pick = [(m, w) for m, w in ((20, 1.0), (22, 1.0), (24, 2.0), (26, 8.0)) if m <= args.n]
+        v, sdesc, tcpu, pts = oracle_sample(args, budget_s=36.0, min_s=24.0, ns=[m for m, _ in pick],
+                                            weights=[w for _, w in pick])
         cpu = {"value": v, "unit": "gates/s", "cores": 1, "host_cores": os.cpu_count(), "kind": "oracle",
                "sample": sdesc, "points": pts}
 
