@@ -19,6 +19,7 @@ struct TcArgs {
     uint64_t ntiles;
     long long timeout_ns;
     int skip_mma;                 // test hook: never issue the MMA (the wait must time out)
+    uint8_t epi_mode;             // kernel and epilogue form (k_fused_tc.cu): 0, 1 pipeline; 2 two groups
     uint8_t tile_pos[kTcM];
     uint8_t outer_pos[40];
     uint16_t offL[64];            // tile index offset of block-local index l

@@ -8,29 +8,63 @@
 // always 128 x 128, so one MMA shape (M = 128, N = kTcN = 64, K = 16 per
 // instruction) serves every k <= 6; column n of B holds P groups of d
 // amplitudes.  For k < 6 most of each product multiplies zeros: harmless
-// while the kernel is bound by HBM.
+// while the kernel is bound by memory traffic.
 //
 // Split precision: A = Ah + Al and B = Bh + Bl with BF16 parts (Ah = bf16(A),
 // Al = bf16(A - Ah)); D = Ah Bh + Ah Bl + Al Bh accumulates in FP32 in tensor
 // memory (relative error about 2^-16 per product instead of 2^-8).
 //
-// Per CTA (persistent, one per SM, two groups of 256 threads): A lives in
-// tensor memory (row m in lane m, two BF16 K elements per 32-bit column; A_hi
-// in columns 0-63, A_lo in 64-127, written once), which leaves shared memory
-// to the groups: each has its own B operand, a ring of kTcRing FP32 staging
-// tiles, 64 TMEM accumulator columns, mbarrier and named barrier.  Per tile
-// of 2^12 amplitudes (the k block qubits plus the lowest other qubits; B is
-// 128 x 64) and group:
-//   the tile's cp.async was issued kTcRing - 1 tiles earlier into its ring
-//   slot, and the load kTcRing - 1 tiles ahead goes into the slot freed by
-//   the previous tile now (kTcRing - 1 loads in flight per group) -> convert
-//   to Bh, Bl in the K-major no-swizzle canonical layout -> one thread issues
-//   3 x 8 tcgen05.mma (A from tensor memory) and commits to the group's
-//   mbarrier -> the group waits (bounded by %globaltimer) -> each warp reads
-//   its 32 TMEM lanes with tcgen05.ld and scatters FP32 results back to the
-//   staging tile -> coalesced 16-byte stores to HBM.
-// Timeout: the wait for the MMAs is bounded by %globaltimer.  When it runs
-// out, the group stops, the CTA frees its tensor memory and the host sees
+// Both kernels keep A in tensor memory (row m in lane m, two BF16 K elements
+// per 32-bit column; A_hi in columns 0-63, A_lo in 64-127, written once),
+// with two FP32 accumulators of 64 columns after it, and work on tiles of
+// 2^12 amplitudes: the k block qubits plus the lowest other qubits, so tile
+// bits 0..5 are always state qubits 0..5 and B is 128 x 64.  The host picks
+// the kernel per launch from the qubit layout (TcArgs::epi_mode):
+//
+// k_fused_tc, a warp-specialised pipeline over a ring of four FP32 staging
+// tiles, when the accumulator's columns or its rows run along the low
+// qubits (every k = 6 block without qubit 0, or with qubits 0..3):
+//   loader warps (3): cp.async of a tile into a ring slot, 16 bytes per copy
+//     (the slot's mbarrier counts each loader thread once its copies have
+//     landed: cp.async.mbarrier.arrive);
+//   converter warps (8): BF16 hi / lo split of a slot into one of two B
+//     operands (K-major no-swizzle canonical layout), after which the slot
+//     is free for the next load;
+//   MMA thread: 3 x 8 tcgen05.mma into one of the two accumulators,
+//     committed to the B operand's and the accumulator's mbarriers;
+//   epilogue warps (4, one per 32 tensor-memory lanes): tcgen05.ld of the
+//     accumulator, re / im of each amplitude joined by one shuffle, then to
+//     HBM: through a padded per-warp buffer, half the columns at a time,
+//     each store instruction writing whole rows (form 0: columns 0..7 are
+//     qubits 0..2), or straight from the registers, 8 bytes per lane (form
+//     1: each warp's 16 rows are qubits 0..3).
+// In steady state the loads of the next tiles, the split of one, the MMAs
+// of another and the epilogue of a third run at once.
+//
+// k_fused_tc_groups otherwise (k < 6, or qubit 0 in the block among others
+// far apart): two groups of 256 threads per CTA, each with its own B
+// operand, ring of two staging tiles, accumulator, mbarrier and named
+// barrier; per tile and group: the tile's cp.async was issued one tile
+// earlier -> split into Bh, Bl -> one thread issues the 3 x 8 MMAs and
+// commits -> the group waits (bounded) -> tcgen05.ld, scattered back into
+// the staging tile -> coalesced 16-byte stores.
+//
+// Measured (26 qubits, 6-qubit blocks, per launch): blocks {0..5} 224 us in
+// the pipeline (form 1) against 263 us in two groups; {20..25} 238 us (form
+// 0) against 255; a mixed block whose columns start with qubits 0..2 257
+// against 265.  Alternatives measured and dropped: bulk copies
+// (cp.async.bulk) of the tile's 512-byte runs by one producer warp, in and
+// out (about 2.1x slower: 64 copies each way per tile kept the copy engine
+// busy about 75 cycles per copy); results written back into the slot and
+// stored by two loader warps (1.2x slower); six loader and four converter
+// warps (1.3x slower: the loads issue sooner but wait longer in the memory
+// pipeline); for the other layouts, the pipeline with the results written
+// through a shared write-back tile and a three-slot ring (about 330 us per
+// launch, 1.2-1.3x slower than two groups) or straight from the registers
+// (up to 2.6x slower: 8-byte pieces far apart).
+// Timeout: every wait is bounded by %globaltimer; the first to run out
+// raises a flag that ends every role's loop, the loaders wait for their
+// copies in flight, the CTA frees its tensor memory and the host sees
 // SV_ERR_TIMEOUT.  The test hook (skip_mma) issues no MMA, so nothing is in
 // flight then.  After a real timeout the committed MMAs may still be writing
 // the freed tensor memory and may later arrive on an mbarrier in shared
@@ -52,19 +86,20 @@
 namespace sv {
 namespace {
 
+constexpr int kTcACols = 64;                   // TMEM columns of one 128 x 128 BF16 A operand
+constexpr int kTcAccs = 2;                     // accumulators (tiles between MMA and epilogue)
+// A_hi, A_lo and the accumulators, in an allocation of a power of two
+constexpr int kTcCols = 256;
+static_assert(2 * kTcACols + kTcAccs * kTcN <= kTcCols, "tensor memory allocation");
+constexpr uint32_t kBBytes = kTcN * 128 * 2;   // one BF16 B operand (16 KiB)
+constexpr uint32_t kStageBytes = (1u << kTcM) * 8;  // one FP32 staging tile (32 KiB)
+// two-group kernel: staging tiles per group (kTcRing - 1 loads in flight);
+// two fill the shared memory of two groups.  (2^11-amplitude tiles with a
+// ring of five measured slower: the per-tile MMA round trip then dominates.)
 constexpr int kTcGroup = 256;                  // threads of one group
 constexpr int kTcGroups = 2;                   // groups (tiles in flight) per CTA
 constexpr int kTcThreads = kTcGroups * kTcGroup;
-constexpr int kTcACols = 64;                   // TMEM columns of one 128 x 128 BF16 A operand
-// A_hi, A_lo and one accumulator per group, in an allocation of a power of two
-constexpr int kTcCols = 256;
-static_assert(2 * kTcACols + kTcGroups * kTcN <= kTcCols, "tensor memory allocation");
-constexpr uint32_t kOpBytes = 128 * 128 * 2;   // one BF16 A operand image (32 KiB)
-constexpr uint32_t kBBytes = kTcN * 128 * 2;   // one BF16 B operand (16 KiB)
-constexpr uint32_t kStageBytes = (1u << kTcM) * 8;  // one FP32 staging tile (32 KiB)
-// staging tiles per group (kTcRing - 1 loads in flight); two fill the shared
-// memory of two groups.  (2^11-amplitude tiles with a ring of five measured
-// slower: the per-tile MMA round trip then dominates.)
+static_assert(kTcGroups <= kTcAccs, "one accumulator per group");
 constexpr int kTcRing = 2;
 constexpr int kChunkIters = (1 << kTcM) / 2 / kTcGroup;  // 16-byte chunks per thread and tile
 
@@ -73,9 +108,6 @@ __device__ __forceinline__ uint32_t smem_u32(const void *p) { return uint32_t(__
 __device__ __forceinline__ void cp_async16(uint32_t saddr, const void *g) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(saddr), "l"(g) : "memory");
 }
-__device__ __forceinline__ void cp_async_wait_all() {
-    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
-}
 // commit this thread's copies issued since the last commit as one group, then
 // wait until at most kTcRing - 1 groups (the newest) are still in flight
 __device__ __forceinline__ void cp_async_commit_wait_ring() {
@@ -83,11 +115,9 @@ __device__ __forceinline__ void cp_async_commit_wait_ring() {
 }
 // barrier of one 256-thread group (named barrier 1 + g)
 __device__ __forceinline__ void group_sync(int g) { asm volatile("bar.sync %0, 256;\n" ::"r"(1 + g) : "memory"); }
-
 // Staging tile layout: 16-byte chunk c (amplitudes 2c, 2c+1) lives at chunk
-// c ^ ((c>>3 ^ c>>6 ^ c>>9) & 7), which spreads both the B-operand reads
-// (lanes along group bits) and the accumulator writes (lanes along block
-// bits) over the banks.
+// c ^ ((c>>3 ^ c>>6 ^ c>>9) & 7), which spreads the B-operand reads (lanes
+// along group bits, which may lie above the low run) over the banks.
 __device__ __forceinline__ uint32_t swz(uint32_t c) { return c ^ (((c >> 3) ^ (c >> 6) ^ (c >> 9)) & 7u); }
 __device__ __forceinline__ uint32_t sxpos(uint32_t j) { return (swz(j >> 1) << 1) | (j & 1u); }
 
@@ -163,7 +193,7 @@ __device__ __forceinline__ void tmem_ld_half(uint32_t taddr, float *v) {
     for (int i = 0; i < kTcN / 2; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__global__ void __launch_bounds__(kTcThreads, 1) k_fused_tc(float2 *__restrict__ psi, const uint4 *__restrict__ gA,
+__global__ void __launch_bounds__(kTcThreads, 1) k_fused_tc_groups(float2 *__restrict__ psi, const uint4 *__restrict__ gA,
                                                             int *__restrict__ err, const TcArgs a) {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(8) uint64_t mbar[kTcGroups];
@@ -385,6 +415,342 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fused_tc(float2 *__restrict__
     }
 }
 
+// ------------------------------------------------------------------------
+// The pipeline's shape.  Staging slots use the layout above (XOR-linear in
+// the tile index: table entries of disjoint bits combine by XOR).
+constexpr int kPipeStages = 4;                      // ring slots
+constexpr int kPipeBBufs = 2;                       // B operands (hi + lo each)
+// with the MMA warp 16 warps: 4 per SM sub-partition (128 registers)
+constexpr int kConvWarps = 8, kEpiWarps = 4, kLoadWarps = 3;
+constexpr int kConvThreads = 32 * kConvWarps, kLoadThreads = 32 * kLoadWarps;
+constexpr int kPipeThreads = 32 * (kConvWarps + kEpiWarps + kLoadWarps + 1);  // + MMA warp
+constexpr int kLoadWarp0 = kConvWarps + kEpiWarps, kMmaWarp = kLoadWarp0 + kLoadWarps;
+constexpr int kTileChunks = (1 << kTcM) / 2;        // 16-byte chunks of a tile
+constexpr int kLoadIters = (kTileChunks + kLoadThreads - 1) / kLoadThreads;  // per loader thread (the last partly)
+constexpr int kEpiRowPitch = 34;                    // float2 per row of the epilogue buffer (16-byte rows, turned banks)
+constexpr uint32_t kEpiBufBytes = 16 * kEpiRowPitch * 8;  // 16 rows (amplitudes) of one epilogue warp
+constexpr size_t kPipeSmem =
+    size_t(kPipeBBufs) * 2 * kBBytes + size_t(kPipeStages) * kStageBytes + size_t(kEpiWarps) * kEpiBufBytes;
+static_assert(kTcN == 64, "the pipelined epilogue reads 64 accumulator columns");
+static_assert(kConvThreads % kTcN == 0, "fixed B row per converter thread");
+
+// try_wait with a suspend-time hint: the thread sleeps until the phase
+// completes or about 20 us pass (no spinning that would take issue slots
+// from the working warps), then checks the abort flag and its own limit.
+__device__ __forceinline__ bool pipe_wait(uint32_t addr, uint32_t parity, long long timeout_ns, volatile int *abort) {
+    const uint64_t t0 = globaltimer();
+    for (;;) {
+        uint32_t done;
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\nselp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(addr), "r"(parity), "r"(20000u)
+            : "memory");
+        if (done) return true;
+        if (*abort) return false;
+        if (globaltimer() - t0 > uint64_t(timeout_ns)) {
+            *abort = 1;
+            return false;
+        }
+    }
+}
+
+// A wait every lane of a warp leaves with the same answer (lane 0 polls):
+// the roles that follow use warp-wide (.aligned, shuffle) instructions.
+__device__ __forceinline__ bool pipe_wait_warp(uint32_t addr, uint32_t parity, long long timeout_ns,
+                                               volatile int *abort, int lane) {
+    uint32_t ok = 0;
+    if (lane == 0) ok = pipe_wait(addr, parity, timeout_ns, abort) ? 1u : 0u;
+    return __shfl_sync(0xffffffffu, ok, 0) != 0u;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t addr, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(addr), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t addr) {
+    asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(addr) : "memory");
+}
+// the barrier counts this thread once all its earlier cp.async have landed
+__device__ __forceinline__ void mbar_arrive_on_copies(uint32_t addr) {
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];\n" ::"r"(addr) : "memory");
+}
+
+// 64 consecutive 32-bit columns of this warp's 32 lanes (two loads and the
+// wait in one statement: no use of the registers can move above the wait)
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, float *v) {
+    uint32_t r[64];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,"
+        "%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%64];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,%48,"
+        "%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%65];\n"
+        "tcgen05.wait::ld.sync.aligned;\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+          "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]),
+          "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]),
+          "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]),
+          "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]), "=r"(r[56]),
+          "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
+        : "r"(taddr), "r"(taddr + 32u)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 64; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__global__ void __launch_bounds__(kPipeThreads, 1) k_fused_tc(float2 *__restrict__ psi, const uint4 *__restrict__ gA,
+                                                              int *__restrict__ err, const TcArgs a) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    // mbarriers: full[s], sfree[s] (slots), bfull[b], bempty[b] (B operands),
+    // afull[c], aempty[c] (accumulators)
+    __shared__ __align__(8) uint64_t mbar[2 * kPipeStages + 8];
+    __shared__ uint32_t tmem_slot;
+    __shared__ int abort_flag;
+    __shared__ uint16_t tN[kTcN], tK[64];                  // staging positions of n and of K pairs
+    __shared__ uint64_t gN[kTcN];                          // global offset of column n
+    __shared__ uint64_t tB[4][256];                        // global offset of each byte of the tile number
+    __shared__ uint64_t gCL[64], gCH[kTileChunks / 64];    // global offset of chunk bits 0..5 and 6..10
+    __shared__ uint16_t sCL[64], sCH[kTileChunks / 64];    // staging chunk of the same
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    unsigned char *sB = smem;                                         // kPipeBBufs x (hi, lo)
+    unsigned char *sSlots = smem + size_t(kPipeBBufs) * 2 * kBBytes;  // kPipeStages staging tiles
+    unsigned char *sEpi = sSlots + size_t(kPipeStages) * kStageBytes;  // one buffer per epilogue warp
+    const uint32_t bar0 = smem_u32(&mbar[0]);
+    auto full = [&](int s) { return bar0 + 8u * uint32_t(s); };
+    auto sfree = [&](int s) { return bar0 + 8u * uint32_t(kPipeStages + s); };
+    auto bfull = [&](int b) { return bar0 + 8u * uint32_t(2 * kPipeStages + b); };
+    auto bempty = [&](int b) { return bar0 + 8u * uint32_t(2 * kPipeStages + 2 + b); };
+    auto afull = [&](int c) { return bar0 + 8u * uint32_t(2 * kPipeStages + 4 + c); };
+    auto aempty = [&](int c) { return bar0 + 8u * uint32_t(2 * kPipeStages + 6 + c); };
+    volatile int *abort_p = &abort_flag;
+
+    // global offset of a tile index (its bit q is state qubit tile_pos[q])
+    auto gofs = [&](uint32_t j) {
+        uint64_t g = 0;
+        for (int q = 0; q < kTcM; ++q)
+            if (j >> q & 1) g |= uint64_t(1) << a.tile_pos[q];
+        return g;
+    };
+    for (int i = tid; i < 64; i += kPipeThreads) {
+        tN[i] = uint16_t(sxpos(a.offN[i]));
+        gN[i] = gofs(a.offN[i]);
+        const int kk = 2 * i, klg = a.k + 1, rm = (2 << a.k) - 1;  // K elements 2i, 2i + 1
+        tK[i] = uint16_t(sxpos(uint32_t(a.offL[(kk & rm) >> 1] ^ a.offP[kk >> klg])));
+        gCL[i] = gofs(uint32_t(i) << 1);  // chunk c: amplitudes 2c, 2c + 1
+        sCL[i] = uint16_t(swz(uint32_t(i)));
+        if (i < kTileChunks / 64) {
+            gCH[i] = gofs(uint32_t(i) << 7);
+            sCH[i] = uint16_t(swz(uint32_t(i) << 6));
+        }
+    }
+    for (int i = tid; i < 4 * 256; i += kPipeThreads) {  // the tile number's outer bits (tile numbers < 2^32)
+        const int byte = i >> 8, v = i & 255;
+        uint64_t off = 0;
+        for (int b = 0; b < 8; ++b) {
+            const int q = 8 * byte + b;
+            if ((v >> b & 1) && q < a.nouter) off |= uint64_t(1) << a.outer_pos[q];
+        }
+        tB[byte][v] = off;
+    }
+    if (tid == 0) {
+        abort_flag = 0;
+        for (int s = 0; s < kPipeStages; ++s) {
+            mbar_init(full(s), kLoadThreads);
+            mbar_init(sfree(s), kConvThreads);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(bfull(b), kConvThreads);
+            mbar_init(bempty(b), 1);
+            mbar_init(afull(b), 1);
+            mbar_init(aempty(b), 32 * kEpiWarps);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(kTcCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    // A operands into tensor memory once: warp w < 8 writes lanes
+    // 32 (w % 4) .. +31 of A_hi (w < 4) or A_lo (w >= 4)
+    if (warp < 8) {
+        const int q = warp & 3, h = warp >> 2, m = 32 * q + lane;
+        uint32_t r[64];
+        const uint4 *src = gA + (size_t(h) * 128 * 128 * 2 + size_t(m) * 256) / 16;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const uint4 v = src[i];
+            r[4 * i] = v.x;
+            r[4 * i + 1] = v.y;
+            r[4 * i + 2] = v.z;
+            r[4 * i + 3] = v.w;
+        }
+        tmem_st64(tmem_slot + (uint32_t(32 * q) << 16) + uint32_t(kTcACols * h), r);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+
+    const uint64_t grid = gridDim.x;
+    const uint64_t count = (a.ntiles - blockIdx.x + grid - 1) / grid;  // tiles of this CTA (blockIdx.x < ntiles)
+    const long long tmo = a.timeout_ns;
+    auto tile_base = [&](uint64_t i) {
+        const uint64_t tile = blockIdx.x + i * grid;
+        return tB[0][tile & 255] | tB[1][(tile >> 8) & 255] | tB[2][(tile >> 16) & 255] | tB[3][(tile >> 24) & 255];
+    };
+
+    if (warp < kConvWarps) {
+        // ---------------- converters: staging tile -> B operand (BF16 hi, lo)
+        const int lt = tid;
+        const uint32_t sn = tN[lt & (kTcN - 1)];  // a thread's B row is the same in all its tasks
+        for (uint64_t i = 0; i < count; ++i) {
+            const int s = int(i % kPipeStages), b = int(i & 1);
+            if (!pipe_wait_warp(full(s), uint32_t(i / kPipeStages) & 1u, tmo, abort_p, lane)) break;
+            if (i >= 2 && !pipe_wait_warp(bempty(b), uint32_t((i >> 1) - 1) & 1u, tmo, abort_p, lane)) break;
+            const float2 *sX = reinterpret_cast<const float2 *>(sSlots + size_t(s) * kStageBytes);
+            unsigned char *bh = sB + size_t(b) * 2 * kBBytes, *bl = bh + kBBytes;
+#pragma unroll
+            for (int t = lt; t < 16 * kTcN; t += kConvThreads) {
+                const int nrow = t & (kTcN - 1), q8 = t / kTcN;
+                uint32_t hw[4], lw[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {  // K elements 8 q8 + 2e, +1: re and im of one amplitude
+                    const float2 amp = sX[sn ^ tK[q8 * 4 + e]];
+                    const __nv_bfloat162 hi = __float22bfloat162_rn(amp);
+                    const float2 hf = __bfloat1622float2(hi);
+                    const __nv_bfloat162 lo = __float22bfloat162_rn(make_float2(amp.x - hf.x, amp.y - hf.y));
+                    hw[e] = *reinterpret_cast<const uint32_t *>(&hi);
+                    lw[e] = *reinterpret_cast<const uint32_t *>(&lo);
+                }
+                const uint32_t off = uint32_t((nrow & 7) * 16 + q8 * 128 + (nrow >> 3) * 2048);
+                *reinterpret_cast<uint4 *>(bh + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                *reinterpret_cast<uint4 *>(bl + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+            }
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // generic writes -> tensor core reads
+            mbar_arrive(bfull(b));
+            mbar_arrive(sfree(s));
+        }
+    } else if (warp < kLoadWarp0) {
+        // ---------------- epilogue: accumulator -> HBM
+        const int eq = warp & 3;  // tensor-memory lanes 32 eq .. +31 (warp % 4)
+        const int row = 32 * eq + lane;
+        const int klog = a.k + 1, rmask = (2 << a.k) - 1;
+        const uint64_t grow = gofs(uint32_t(a.offL[(row & rmask) >> 1] ^ a.offP[row >> klog]));
+        const int odd = row & 1;  // odd rows hold Im, even rows Re (of the same amplitude as row ^ 1)
+        const int mode = a.epi_mode;
+        for (uint64_t i = 0; i < count; ++i) {
+            const int c = int(i & 1);
+            if (!pipe_wait_warp(afull(c), uint32_t(i >> 1) & 1u, tmo, abort_p, lane)) break;
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            float v[64];
+            tmem_ld64(tmem_slot + (uint32_t(32 * eq) << 16) + uint32_t(2 * kTcACols + c * kTcN), v);
+            asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+            mbar_arrive(aempty(c));
+            const uint64_t tb = tile_base(i);
+            if (mode == 0) {
+                // two rounds of half the columns: the even lane of a pair takes
+                // columns 16h + t, the odd lane 32 + 16h + (t ^ 1) (turned: the
+                // pair's two 8-byte writes fall in different banks); buffer row
+                // r = lane / 2 (the warp's 16 amplitudes), slots 0..15 even, 16..31 odd
+                float2 *buf = reinterpret_cast<float2 *>(sEpi + size_t(eq) * kEpiBufBytes);
+                const int r = lane >> 1;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+#pragma unroll
+                    for (int t = 0; t < 16; ++t) {
+                        const int ce = 16 * h + t, co = 32 + 16 * h + (t ^ 1);
+                        const float got = __shfl_xor_sync(0xffffffffu, odd ? v[ce] : v[co], 1);
+                        if (odd)
+                            buf[r * kEpiRowPitch + 16 + (t ^ 1)] = make_float2(got, v[co]);
+                        else
+                            buf[r * kEpiRowPitch + t] = make_float2(v[ce], got);
+                    }
+                    __syncwarp();
+                    // store: lanes 0..15 row 2 ii, lanes 16..31 row 2 ii + 1; lane
+                    // L & 15 takes slots 2u, 2u + 1 (u = L & 7), even part for L & 8 = 0
+#pragma unroll
+                    for (int ii = 0; ii < 8; ++ii) {
+                        const int rr = 2 * ii + (lane >> 4), u = lane & 15;
+                        const uint64_t gr = __shfl_sync(0xffffffffu, grow, 2 * rr);
+                        const float4 val = *reinterpret_cast<const float4 *>(buf + rr * kEpiRowPitch + 2 * u);
+                        const int col = (u < 8 ? 16 * h : 32 + 16 * h - 16) + 2 * u;
+                        *reinterpret_cast<float4 *>(psi + (tb | gr | gN[col])) = val;
+                    }
+                    __syncwarp();
+                }
+            } else {
+                float2 *g = psi + (tb | grow);
+                const int c0 = odd ? 32 : 0;
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const float got = __shfl_xor_sync(0xffffffffu, odd ? v[j] : v[32 + j], 1);
+                    g[gN[c0 + j]] = odd ? make_float2(got, v[32 + j]) : make_float2(v[j], got);
+                }
+            }
+        }
+    } else if (warp < kMmaWarp) {
+        // ---------------- loaders: HBM -> staging tiles, 16-byte chunks
+        // chunk c = lt + kLoadThreads r of a tile (amplitudes 2c, 2c + 1); a
+        // warp's 32 chunks are 512 contiguous bytes (tile bits 0..5 are state
+        // qubits 0..5, and 32 divides kLoadThreads)
+        const int lt = tid - 32 * kLoadWarp0;
+        for (uint64_t i = 0; i < count; ++i) {
+            const int s = int(i % kPipeStages);
+            if (i >= kPipeStages && !pipe_wait_warp(sfree(s), uint32_t(i / kPipeStages - 1) & 1u, tmo, abort_p, lane))
+                break;
+            float2 *sX = reinterpret_cast<float2 *>(sSlots + size_t(s) * kStageBytes);
+            const float2 *g = psi + tile_base(i);
+#pragma unroll
+            for (int r = 0; r < kLoadIters; ++r) {
+                const int c = lt + kLoadThreads * r;
+                if (c < kTileChunks)
+                    cp_async16(smem_u32(sX + 2 * (sCL[c & 63] ^ sCH[c >> 6])), g + (gCL[c & 63] | gCH[c >> 6]));
+            }
+            mbar_arrive_on_copies(full(s));
+        }
+        asm volatile("cp.async.wait_all;\n" ::: "memory");  // no copy still writing when the CTA leaves
+    } else if (lane == 0) {
+        // ---------------- MMA issue
+        const uint32_t tA = tmem_slot;
+        for (uint64_t i = 0; i < count; ++i) {
+            const int b = int(i & 1), c = int(i & 1);
+            if (!pipe_wait(bfull(b), uint32_t(i >> 1) & 1u, tmo, abort_p)) break;
+            if (i >= 2 && !pipe_wait(aempty(c), uint32_t((i >> 1) - 1) & 1u, tmo, abort_p)) break;
+            if (a.skip_mma) continue;  // test hook: no MMA, no commit (the epilogue's wait runs out)
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            const uint32_t bh = smem_u32(sB + size_t(b) * 2 * kBBytes), bl = bh + kBBytes;
+            const uint32_t tD = tA + uint32_t(2 * kTcACols + c * kTcN);
+            uint32_t acc = 0;
+#pragma unroll
+            for (int pass = 0; pass < 3; ++pass) {
+                const uint32_t aa = tA + uint32_t(pass == 2 ? kTcACols : 0), bb = pass == 1 ? bl : bh;
+#pragma unroll
+                for (int ks = 0; ks < 8; ++ks) {
+                    mma_bf16_ts(tD, aa + 8u * ks, sdesc(bb + 256u * ks, 128, 2048), acc);
+                    acc = 1;
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bempty(b))
+                         : "memory");
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(afull(c))
+                         : "memory");
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (tid == 0 && abort_flag) atomicExch(err, int(SV_ERR_TIMEOUT));
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem_slot), "r"(kTcCols)
+                     : "memory");
+    }
+}
+
 uint16_t bf16_rne_host(float f) {
     uint32_t u;
     std::memcpy(&u, &f, 4);
@@ -473,6 +839,19 @@ void tc_prepare(int n, int k, const int *qubits, const double *U, uint16_t *a_op
     }
     a.ntiles = uint64_t(1) << (n - kTcM);
     a.timeout_ns = 2000000000LL;
+    // kernel and epilogue form: tile bits 0..3 are state qubits 0..3, so
+    // "columns 0..7 are qubits 0..2" means offN[c] = c, and "each epilogue
+    // warp's 16 rows are qubits 0..3" means the row amplitudes' tile bits
+    // 0..3 count 0..15; with neither, the two-group kernel (epi_mode 2)
+    bool cols = true, rows = true;
+    for (int c = 0; c < 8; ++c) cols = cols && a.offN[c] == c;
+    for (int w = 0; w < 4 && rows; ++w)
+        for (int r = 0; r < 16; ++r) {
+            const int row = 32 * w + 2 * r;
+            const uint32_t j = uint32_t(a.offL[(row & (2 * d - 1)) >> 1] ^ a.offP[row >> (k + 1)]);
+            rows = rows && (j & 15u) == uint32_t(r);
+        }
+    a.epi_mode = uint8_t(cols ? 0 : (rows ? 1 : 2));
 }
 
 cudaError_t tc_launch(sv_state *h, const TcArgs &args, const void *dA) {
@@ -485,20 +864,29 @@ cudaError_t tc_launch(sv_state *h, const TcArgs &args, const void *dA) {
         const cudaError_t e = ensure_err_word(h);
         if (e != cudaSuccess) return e;
     }
-    const size_t smem = kTcGroups * (2 * size_t(kBBytes) + kTcRing * size_t(kStageBytes));
+    const size_t smem_groups = kTcGroups * (2 * size_t(kBBytes) + kTcRing * size_t(kStageBytes));
     static std::atomic<uint64_t> configured{0};
     if (attrs_needed(configured, h->device)) {
-        const cudaError_t e = cudaFuncSetAttribute(k_fused_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        cudaError_t e = cudaFuncSetAttribute(k_fused_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kPipeSmem));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_fused_tc_groups, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     int(smem_groups));
         if (e != cudaSuccess) return e;
         attrs_set(configured, h->device);
     }
     int sms = 0;
     const cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
     if (e != cudaSuccess) return e;
-    const uint64_t sets = (a.ntiles + kTcGroups - 1) / kTcGroups;  // kTcGroups tiles in flight per CTA
-    const uint64_t grid = sets < uint64_t(sms) ? sets : uint64_t(sms);
-    k_fused_tc<<<unsigned(grid), kTcThreads, smem, h->stream>>>(static_cast<float2 *>(h->data),
-                                                                static_cast<const uint4 *>(dA), h->d_err, a);
+    if (a.epi_mode <= 1) {  // the pipeline: columns or rows run along the low qubits
+        const uint64_t grid = a.ntiles < uint64_t(sms) ? a.ntiles : uint64_t(sms);
+        k_fused_tc<<<unsigned(grid), kPipeThreads, kPipeSmem, h->stream>>>(
+            static_cast<float2 *>(h->data), static_cast<const uint4 *>(dA), h->d_err, a);
+    } else {
+        const uint64_t sets = (a.ntiles + kTcGroups - 1) / kTcGroups;  // kTcGroups tiles in flight per CTA
+        const uint64_t grid = sets < uint64_t(sms) ? sets : uint64_t(sms);
+        k_fused_tc_groups<<<unsigned(grid), kTcThreads, smem_groups, h->stream>>>(
+            static_cast<float2 *>(h->data), static_cast<const uint4 *>(dA), h->d_err, a);
+    }
     return cudaGetLastError();
 }
 

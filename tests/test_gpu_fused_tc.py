@@ -40,6 +40,10 @@ def check_c64(got, ref):
     assert 1 - f <= 1e-5
 
 
+# The sets reach both tensor-core kernels and every epilogue form: blocks
+# holding qubits 0..3 (pipeline, rows along the low qubits), blocks without
+# qubit 0 at k = 6 (pipeline, columns along the low qubits), and the rest
+# (two-group kernel: k < 6 with far-apart qubits, qubit 0 among far-apart ones).
 QUBIT_SETS = {
     1: [[0], [7], [13]],
     2: [[0, 1], [12, 3], [9, 5]],
