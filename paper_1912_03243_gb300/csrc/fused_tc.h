@@ -20,6 +20,14 @@ struct TcArgs {
     long long timeout_ns;
     int skip_mma;                 // test hook: never issue the MMA (the wait must time out)
     uint8_t epi_mode;             // kernel and epilogue form (k_fused_tc.cu): 0, 1 pipeline; 2 two groups
+    // form 0 loads tiles with tensor-map copies: the tile's qubit ranges as
+    // the map's dimensions (a dimension starts at qubit tma_start[d] and ends
+    // where the next starts; the last ends at n), tma_nbox boxes per tile at
+    // global offsets tma_boff[b] (the top tile runs, when there are more than
+    // the map's five dimensions can hold)
+    uint8_t tma, tma_rank, tma_nbox;
+    uint8_t tma_start[5];
+    uint64_t tma_boff[4];
     uint8_t tile_pos[kTcM];
     uint8_t outer_pos[40];
     uint16_t offL[64];            // tile index offset of block-local index l

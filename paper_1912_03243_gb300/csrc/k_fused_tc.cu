@@ -24,9 +24,12 @@
 // k_fused_tc, a warp-specialised pipeline over a ring of four FP32 staging
 // tiles, when the accumulator's columns or its rows run along the low
 // qubits (every k = 6 block without qubit 0, or with qubits 0..3):
-//   loader warps (3): cp.async of a tile into a ring slot, 16 bytes per copy
-//     (the slot's mbarrier counts each loader thread once its copies have
-//     landed: cp.async.mbarrier.arrive);
+//   loads: tensor-map copies (cp.async.bulk.tensor, 128-byte swizzle) by one
+//     thread, counted in bytes on the slot's mbarrier, when the columns run
+//     along the low qubits (form 0: the split's lanes along qubits 0..4 then
+//     meet no bank conflicts in the swizzled rows); otherwise 3 loader warps
+//     with 16-byte cp.async (the slot's mbarrier counts each loader thread
+//     once its copies have landed: cp.async.mbarrier.arrive);
 //   converter warps (8): BF16 hi / lo split of a slot into one of two B
 //     operands (K-major no-swizzle canonical layout), after which the slot
 //     is free for the next load;
@@ -49,10 +52,10 @@
 // commits -> the group waits (bounded) -> tcgen05.ld, scattered back into
 // the staging tile -> coalesced 16-byte stores.
 //
-// Measured (26 qubits, 6-qubit blocks, per launch): blocks {0..5} 224 us in
-// the pipeline (form 1) against 263 us in two groups; {20..25} 238 us (form
-// 0) against 255; a mixed block whose columns start with qubits 0..2 257
-// against 265.  Alternatives measured and dropped: bulk copies
+// Measured (26 qubits, 6-qubit blocks, per launch): blocks {0..5} 221 us in
+// the pipeline (form 1) against 263 us in two groups; {20..25} 221 us (form
+// 0, tensor-map loads; 240 with cp.async) against 255; a mixed block whose
+// columns start with qubits 0..2 232 (258) against 265.  Alternatives measured and dropped: bulk copies
 // (cp.async.bulk) of the tile's 512-byte runs by one producer warp, in and
 // out (about 2.1x slower: 64 copies each way per tile kept the copy engine
 // busy about 75 cycles per copy); results written back into the slot and
@@ -75,6 +78,7 @@
 // offset 128 (next 8 K-elements), stride-dimension byte offset 2048 (next 8
 // rows); the K-slice s of an instruction starts at + 256 s (and at column
 // + 8 s of A in tensor memory).
+#include <cuda.h>  // CUtensorMap and its encoder's types (the encoder is fetched at run time, not linked)
 #include <cuda_bf16.h>
 
 #include <cstring>
@@ -455,6 +459,25 @@ __device__ __forceinline__ bool pipe_wait(uint32_t addr, uint32_t parity, long l
     }
 }
 
+// Position (in amplitudes) of tile index j in a slot filled by tensor-map
+// copies with the 128-byte swizzle: the 16-byte chunk (j bits 1..3) is
+// XORed with the 128-byte row modulo 8 (j bits 4..6).  XOR-linear in j.
+__host__ __device__ constexpr uint32_t tma_pos(uint32_t j) { return j ^ (((j >> 4) & 7u) << 1); }
+
+// one box of the tensor map at coordinates c into shared memory, counted in
+// bytes on the mbarrier
+__device__ __forceinline__ void tma_load5(uint32_t dst, const CUtensorMap *map, const int32_t (&c)[5], uint32_t mbar) {
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, "
+        "%6}], [%7];\n" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(c[3]), "r"(c[4]), "r"(mbar)
+        : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t addr, uint32_t bytes) {
+    asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(addr), "r"(bytes)
+                 : "memory");
+}
+
 // A wait every lane of a warp leaves with the same answer (lane 0 polls):
 // the roles that follow use warp-wide (.aligned, shuffle) instructions.
 __device__ __forceinline__ bool pipe_wait_warp(uint32_t addr, uint32_t parity, long long timeout_ns,
@@ -500,7 +523,8 @@ __device__ __forceinline__ void tmem_ld64(uint32_t taddr, float *v) {
 }
 
 __global__ void __launch_bounds__(kPipeThreads, 1) k_fused_tc(float2 *__restrict__ psi, const uint4 *__restrict__ gA,
-                                                              int *__restrict__ err, const TcArgs a) {
+                                                              int *__restrict__ err, const TcArgs a,
+                                                              const __grid_constant__ CUtensorMap tmap) {
     extern __shared__ __align__(1024) unsigned char smem[];
     // mbarriers: full[s], sfree[s] (slots), bfull[b], bempty[b] (B operands),
     // afull[c], aempty[c] (accumulators)
@@ -533,10 +557,11 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_fused_tc(float2 *__restrict
         return g;
     };
     for (int i = tid; i < 64; i += kPipeThreads) {
-        tN[i] = uint16_t(sxpos(a.offN[i]));
+        tN[i] = uint16_t(a.tma ? tma_pos(a.offN[i]) : sxpos(a.offN[i]));
         gN[i] = gofs(a.offN[i]);
         const int kk = 2 * i, klg = a.k + 1, rm = (2 << a.k) - 1;  // K elements 2i, 2i + 1
-        tK[i] = uint16_t(sxpos(uint32_t(a.offL[(kk & rm) >> 1] ^ a.offP[kk >> klg])));
+        const uint32_t jk = uint32_t(a.offL[(kk & rm) >> 1] ^ a.offP[kk >> klg]);
+        tK[i] = uint16_t(a.tma ? tma_pos(jk) : sxpos(jk));
         gCL[i] = gofs(uint32_t(i) << 1);  // chunk c: amplitudes 2c, 2c + 1
         sCL[i] = uint16_t(swz(uint32_t(i)));
         if (i < kTileChunks / 64) {
@@ -556,7 +581,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_fused_tc(float2 *__restrict
     if (tid == 0) {
         abort_flag = 0;
         for (int s = 0; s < kPipeStages; ++s) {
-            mbar_init(full(s), kLoadThreads);
+            mbar_init(full(s), a.tma ? 1u : uint32_t(kLoadThreads));
             mbar_init(sfree(s), kConvThreads);
         }
         for (int b = 0; b < 2; ++b) {
@@ -694,26 +719,70 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_fused_tc(float2 *__restrict
             }
         }
     } else if (warp < kMmaWarp) {
-        // ---------------- loaders: HBM -> staging tiles, 16-byte chunks
-        // chunk c = lt + kLoadThreads r of a tile (amplitudes 2c, 2c + 1); a
-        // warp's 32 chunks are 512 contiguous bytes (tile bits 0..5 are state
-        // qubits 0..5, and 32 divides kLoadThreads)
+        // ---------------- loaders: HBM -> staging tiles
         const int lt = tid - 32 * kLoadWarp0;
-        for (uint64_t i = 0; i < count; ++i) {
-            const int s = int(i % kPipeStages);
-            if (i >= kPipeStages && !pipe_wait_warp(sfree(s), uint32_t(i / kPipeStages - 1) & 1u, tmo, abort_p, lane))
-                break;
-            float2 *sX = reinterpret_cast<float2 *>(sSlots + size_t(s) * kStageBytes);
-            const float2 *g = psi + tile_base(i);
+        if (a.tma) {
+            // one thread: a.tma_nbox tensor-map boxes per tile (each of the
+            // map's dimensions holds a range of qubits: the box's coordinate
+            // is that range of the box's global offset)
+            if (lt == 0) {
+                uint64_t issued[kPipeStages] = {0, 0, 0, 0};
+                const uint32_t box_bytes = kStageBytes / a.tma_nbox;
+                for (uint64_t i = 0; i < count; ++i) {
+                    const int s = int(i % kPipeStages);
+                    if (i >= kPipeStages && !pipe_wait(sfree(s), uint32_t(i / kPipeStages - 1) & 1u, tmo, abort_p)) break;
+                    mbar_expect_tx(full(s), kStageBytes);
+                    const uint32_t dst = smem_u32(sSlots + size_t(s) * kStageBytes);
+                    const uint64_t tb = tile_base(i);
+                    for (int b = 0; b < a.tma_nbox; ++b) {
+                        const uint64_t g = tb | a.tma_boff[b];
+                        int32_t c[5];
 #pragma unroll
-            for (int r = 0; r < kLoadIters; ++r) {
-                const int c = lt + kLoadThreads * r;
-                if (c < kTileChunks)
-                    cp_async16(smem_u32(sX + 2 * (sCL[c & 63] ^ sCH[c >> 6])), g + (gCL[c & 63] | gCH[c >> 6]));
+                        for (int d = 0; d < 5; ++d) {
+                            const int lo = a.tma_start[d], hi = d + 1 < a.tma_rank ? a.tma_start[d + 1] : a.n;
+                            c[d] = d < a.tma_rank ? int32_t((g >> lo) & ((uint64_t(1) << (hi - lo)) - 1u)) : 0;
+                        }
+                        tma_load5(dst + uint32_t(b) * box_bytes, &tmap, c, full(s));
+                    }
+                    ++issued[s];
+                }
+                if (*abort_p)  // copies still in flight land before the CTA leaves
+                    for (int s = 0; s < kPipeStages; ++s)
+                        if (issued[s]) {
+                            const uint64_t t0 = globaltimer();
+                            uint32_t done = 0;
+                            while (!done && globaltimer() - t0 < uint64_t(tmo)) {
+                                asm volatile(
+                                    "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 "
+                                    "%0, 1, 0, p;\n}\n"
+                                    : "=r"(done)
+                                    : "r"(full(s)), "r"(uint32_t(issued[s] - 1) & 1u)
+                                    : "memory");
+                            }
+                        }
             }
-            mbar_arrive_on_copies(full(s));
+        } else {
+            // 16-byte cp.async: chunk c = lt + kLoadThreads r of a tile
+            // (amplitudes 2c, 2c + 1); a warp's 32 chunks are 512 contiguous
+            // bytes (tile bits 0..5 are state qubits 0..5, and 32 divides
+            // kLoadThreads)
+            for (uint64_t i = 0; i < count; ++i) {
+                const int s = int(i % kPipeStages);
+                if (i >= kPipeStages &&
+                    !pipe_wait_warp(sfree(s), uint32_t(i / kPipeStages - 1) & 1u, tmo, abort_p, lane))
+                    break;
+                float2 *sX = reinterpret_cast<float2 *>(sSlots + size_t(s) * kStageBytes);
+                const float2 *g = psi + tile_base(i);
+#pragma unroll
+                for (int r = 0; r < kLoadIters; ++r) {
+                    const int c = lt + kLoadThreads * r;
+                    if (c < kTileChunks)
+                        cp_async16(smem_u32(sX + 2 * (sCL[c & 63] ^ sCH[c >> 6])), g + (gCL[c & 63] | gCH[c >> 6]));
+                }
+                mbar_arrive_on_copies(full(s));
+            }
+            asm volatile("cp.async.wait_all;\n" ::: "memory");  // no copy still writing when the CTA leaves
         }
-        asm volatile("cp.async.wait_all;\n" ::: "memory");  // no copy still writing when the CTA leaves
     } else if (lane == 0) {
         // ---------------- MMA issue
         const uint32_t tA = tmem_slot;
@@ -852,6 +921,99 @@ void tc_prepare(int n, int k, const int *qubits, const double *U, uint16_t *a_op
             rows = rows && (j & 15u) == uint32_t(r);
         }
     a.epi_mode = uint8_t(cols ? 0 : (rows ? 1 : 2));
+    // form 0 loads with tensor-map copies: runs of consecutive tile qubits
+    // (run 0 starts at qubit 0 and is at least 6 long); the map's dimensions
+    // are qubits 0..3 (128 bytes, the 128-byte swizzle's row), the rest of
+    // run 0, then one per later run, each reaching up to the next; runs
+    // beyond five dimensions (the top ones) are iterated as separate boxes
+    if (a.epi_mode == 0) {
+        int rs[kTcM], rl[kTcM], nr = 0;
+        for (int t = 0; t < kTcM; ++t) {
+            if (t > 0 && a.tile_pos[t] == a.tile_pos[t - 1] + 1) {
+                ++rl[nr - 1];
+            } else {
+                rs[nr] = a.tile_pos[t];
+                rl[nr++] = 1;
+            }
+        }
+        const int boxed = std::min(nr, 4);  // runs 0 .. boxed-1 in the box (run 0 takes two dimensions)
+        int it_bits = 0;
+        for (int r = boxed; r < nr; ++r) it_bits += rl[r];
+        if (rs[0] == 0 && rl[0] >= 6 && it_bits <= 2) {
+            a.tma = 1;
+            a.tma_rank = uint8_t(boxed + 1);
+            a.tma_start[0] = 0;
+            a.tma_start[1] = 4;
+            for (int r = 1; r < boxed; ++r) a.tma_start[r + 1] = uint8_t(rs[r]);
+            a.tma_nbox = uint8_t(1 << it_bits);
+            for (int b = 0; b < a.tma_nbox; ++b) {  // the iterated runs' qubits, ascending, from b's bits
+                uint64_t off = 0;
+                int bit = 0;
+                for (int r = boxed; r < nr; ++r)
+                    for (int q = rs[r]; q < rs[r] + rl[r]; ++q, ++bit)
+                        if (b >> bit & 1) off |= uint64_t(1) << q;
+                a.tma_boff[b] = off;
+            }
+        }
+    }
+}
+
+// cuTensorMapEncodeTiled, looked up once through the runtime (the library
+// links only the static runtime); nullptr if the driver does not offer it.
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled_fn() {
+    static const EncodeTiledFn fn = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            p = nullptr;
+        return reinterpret_cast<EncodeTiledFn>(p);
+    }();
+    return fn;
+}
+
+// The state as a tensor of 8-byte elements whose dimensions are the ranges of
+// qubits TcArgs::tma_start sets out (sizes 2^range, strides the products of
+// the ones below: the plain layout), padded to five dimensions of size 1; the
+// box covers the tile's part of each range; 128-byte swizzle.
+cudaError_t encode_tile_map(void *data, int n, const TcArgs &a, CUtensorMap *map) {
+    const EncodeTiledFn fn = encode_tiled_fn();
+    if (!fn) return cudaErrorNotSupported;
+    cuuint64_t dim[5], stride[4];
+    cuuint32_t box[5], estr[5] = {1, 1, 1, 1, 1};
+    uint64_t bytes = 8;  // stride of the current dimension
+    for (int d = 0; d < 5; ++d) {
+        if (d < a.tma_rank) {
+            const int lo = a.tma_start[d], hi = d + 1 < a.tma_rank ? a.tma_start[d + 1] : n;
+            dim[d] = cuuint64_t(1) << (hi - lo);
+            int in_tile = 0;  // tile qubits in [lo, hi): qubits 0..3, the rest of run 0, or a run (and iterated ones)
+            for (int t = 0; t < kTcM; ++t) in_tile += a.tile_pos[t] >= lo && a.tile_pos[t] < hi;
+            box[d] = cuuint32_t(1) << in_tile;
+        } else {
+            dim[d] = 1;
+            box[d] = 1;
+        }
+        if (d > 0) stride[d - 1] = bytes;
+        bytes *= dim[d];
+    }
+    // iterated runs lie inside the last range but outside the box
+    {
+        int it = 0;
+        for (int b = a.tma_nbox; b > 1; b >>= 1) ++it;
+        box[a.tma_rank - 1] >>= it;
+    }
+    const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 5, data, dim, stride, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        set_error("cuTensorMapEncodeTiled failed (%d)", int(r));
+        return cudaErrorInvalidValue;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t tc_launch(sv_state *h, const TcArgs &args, const void *dA) {
@@ -878,9 +1040,15 @@ cudaError_t tc_launch(sv_state *h, const TcArgs &args, const void *dA) {
     const cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
     if (e != cudaSuccess) return e;
     if (a.epi_mode <= 1) {  // the pipeline: columns or rows run along the low qubits
+        CUtensorMap map;
+        std::memset(&map, 0, sizeof(map));
+        if (a.tma) {
+            const cudaError_t me = encode_tile_map(h->data, h->n, a, &map);
+            if (me != cudaSuccess) return me;
+        }
         const uint64_t grid = a.ntiles < uint64_t(sms) ? a.ntiles : uint64_t(sms);
         k_fused_tc<<<unsigned(grid), kPipeThreads, kPipeSmem, h->stream>>>(
-            static_cast<float2 *>(h->data), static_cast<const uint4 *>(dA), h->d_err, a);
+            static_cast<float2 *>(h->data), static_cast<const uint4 *>(dA), h->d_err, a, map);
     } else {
         const uint64_t sets = (a.ntiles + kTcGroups - 1) / kTcGroups;  // kTcGroups tiles in flight per CTA
         const uint64_t grid = sets < uint64_t(sms) ? sets : uint64_t(sms);
