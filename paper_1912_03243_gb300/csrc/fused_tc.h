@@ -40,5 +40,7 @@ struct TcArgs {
 void tc_prepare(int n, int k, const int *qubits, const double *U, uint16_t *a_ops, TcArgs *args);
 // Launch with operands already in device memory (dA: kTcOperandBytes).
 cudaError_t tc_launch(sv_state *h, const TcArgs &args, const void *dA);
+// The kernel (and its load form) a launch with these arguments runs.
+const char *tc_kernel_name(const TcArgs &a);
 
 }  // namespace sv

@@ -1058,6 +1058,18 @@ cudaError_t tc_launch(sv_state *h, const TcArgs &args, const void *dA) {
     return cudaGetLastError();
 }
 
+const char *tc_kernel_name(const TcArgs &a) {
+    static const char *names[3][7] = {
+        {"k_fused_tc<k=0>", "k_fused_tc<k=1>", "k_fused_tc<k=2>", "k_fused_tc<k=3>", "k_fused_tc<k=4>",
+         "k_fused_tc<k=5>", "k_fused_tc<k=6>"},
+        {"k_fused_tc<k=0,tma>", "k_fused_tc<k=1,tma>", "k_fused_tc<k=2,tma>", "k_fused_tc<k=3,tma>",
+         "k_fused_tc<k=4,tma>", "k_fused_tc<k=5,tma>", "k_fused_tc<k=6,tma>"},
+        {"k_fused_tc_groups<k=0>", "k_fused_tc_groups<k=1>", "k_fused_tc_groups<k=2>", "k_fused_tc_groups<k=3>",
+         "k_fused_tc_groups<k=4>", "k_fused_tc_groups<k=5>", "k_fused_tc_groups<k=6>"}};
+    const int form = a.epi_mode > 1 ? 2 : (a.tma ? 1 : 0);
+    return names[form][a.k < 0 || a.k > 6 ? 0 : a.k];
+}
+
 cudaError_t launch_fused_tc(sv_state *h, int k, const int *qubits, const double *U) {
     static thread_local std::vector<uint16_t> host;
     host.resize(2 * 128 * 128);

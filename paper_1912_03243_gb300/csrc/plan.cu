@@ -180,9 +180,7 @@ cudaError_t launch_one(sv_plan_s *p, const PlanLaunch &l) {
 
 const char *launch_name(const sv_plan_s *p, const PlanLaunch &l) {
     if (l.kind == 0) return gate1_kernel_name(p->h, p->pergate[size_t(l.index)]);
-    static const char *tc_names[] = {"k_fused_tc<k=0>", "k_fused_tc<k=1>", "k_fused_tc<k=2>", "k_fused_tc<k=3>",
-                                     "k_fused_tc<k=4>", "k_fused_tc<k=5>", "k_fused_tc<k=6>"};
-    if (l.kind == 2) return tc_names[p->tcargs[size_t(l.index)].k];
+    if (l.kind == 2) return tc_kernel_name(p->tcargs[size_t(l.index)]);
     if (l.kind == 3) return p->h->dt == SV_C64 ? "k_fused_dense<f32>" : "k_fused_dense<f64>";
     if (l.kind == 4) return "k_enc_run_in";
     return tile_kernel_name(p->h);
