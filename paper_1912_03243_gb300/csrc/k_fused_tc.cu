@@ -61,7 +61,8 @@
 // busy about 75 cycles per copy); results written back into the slot and
 // stored by two loader warps (1.2x slower); six loader and four converter
 // warps (1.3x slower: the loads issue sooner but wait longer in the memory
-// pipeline); for the other layouts, the pipeline with the results written
+// pipeline); five ring slots with one B operand (1.3x slower: the split then
+// waits for each tile's MMAs); for the other layouts, the pipeline with the results written
 // through a shared write-back tile and a three-slot ring (about 330 us per
 // launch, 1.2-1.3x slower than two groups) or straight from the registers
 // (up to 2.6x slower: 8-byte pieces far apart).
@@ -423,7 +424,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fused_tc_groups(float2 *__res
 // The pipeline's shape.  Staging slots use the layout above (XOR-linear in
 // the tile index: table entries of disjoint bits combine by XOR).
 constexpr int kPipeStages = 4;                      // ring slots
-constexpr int kPipeBBufs = 2;                       // B operands (hi + lo each)
+constexpr int kPipeBBufs = 2;                       // B operands (hi + lo each; the indexing assumes two)
 // with the MMA warp 16 warps: 4 per SM sub-partition (128 registers)
 constexpr int kConvWarps = 8, kEpiWarps = 4, kLoadWarps = 3;
 constexpr int kConvThreads = 32 * kConvWarps, kLoadThreads = 32 * kLoadWarps;
