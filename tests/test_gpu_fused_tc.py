@@ -69,11 +69,10 @@ def test_blocks_14q(S, orc, k):
 
 @pytest.mark.parametrize("n", [12, 13, 14, 20, 22])
 def test_blocks_one_and_many_tiles(S, orc, n):
-    """Tiles hold 2^12 amplitudes; each CTA has two thread groups, each with
-    a ring of staging tiles (the next tile's load in flight): n = 12 is one
-    tile (one group idle), n = 13 two (one CTA, both groups busy once), n =
-    14 four, n = 20 gives 256 tiles, n = 22 1024 (three or four per group:
-    the ring wraps, mbarrier phases alternate)."""
+    """Tiles hold 2^12 amplitudes: n = 12 is one tile (one CTA, most roles
+    idle after one pass), n = 13 two, n = 14 four, n = 20 gives 256 tiles,
+    n = 22 1024 (several per CTA: the staging ring and the accumulators wrap,
+    mbarrier phases alternate)."""
     rng = np.random.default_rng(n)
     psi0 = C.random_state(n, 7 + n)
     s = S.StateVector(n, "c64")
@@ -83,6 +82,38 @@ def test_blocks_one_and_many_tiles(S, orc, n):
         s.from_numpy(psi0)
         s.apply_fused(qs, u)
         check_c64(s.to_numpy(), orc.apply_kq(psi0, qs, u))
+
+
+# (n, qubits) reaching each kernel and load form (the host picks them from the
+# layout): the pipeline with loader warps and rows along the low qubits, the
+# pipeline with loader warps and columns along them (too many qubit runs for
+# the tensor map's five dimensions), the pipeline with tensor-map loads (one
+# box per tile; four boxes when two runs are iterated), and the two-group
+# kernel (qubit 0 among far-apart qubits, k < 6 with far-apart qubits).
+FORMS = [
+    (22, [0, 1, 2, 3, 4, 5]),
+    (14, [0, 1]),
+    (22, [8, 10, 12, 14, 16, 18]),
+    (14, [8, 9, 10, 11, 12, 13]),
+    (20, [14, 15, 16, 17, 18, 19]),
+    (13, [7, 8, 9, 10, 11, 12]),
+    (22, [3, 9, 12, 15, 18, 21]),
+    (14, [0, 9]),
+    (22, [0, 7, 12, 13, 20, 21]),
+    (22, [19, 20, 21]),
+    (22, [0, 9, 14, 20]),
+]
+
+
+@pytest.mark.parametrize("n,qs", FORMS)
+def test_every_kernel_form(S, orc, n, qs):
+    rng = np.random.default_rng(n + len(qs))
+    psi0 = C.random_state(n, 31 + n)
+    u = random_u(rng, 1 << len(qs))
+    s = S.StateVector(n, "c64")
+    s.from_numpy(psi0)
+    s.apply_fused(qs, u)
+    check_c64(s.to_numpy(), orc.apply_kq(psi0, qs, u))
 
 
 def test_block_sequence(S, orc):
@@ -112,16 +143,20 @@ def test_block_sequence(S, orc):
     check_c64(s.to_numpy(), ref)
 
 
-def test_timeout_path_reports_and_recovers(S, monkeypatch):
-    """The tensor-core kernel's only wait (for its MMAs) is bounded by the
-    global timer.  With the host-side hook the MMAs are never issued, the
-    wait runs out after 1 ms, the kernel releases its tensor memory and sets
-    the error word; the next synchronising call reports SV_ERR_TIMEOUT and
-    the context stays usable."""
+@pytest.mark.parametrize("qs", [[0, 1], [8, 9, 10, 11, 12, 13], [0, 9]])
+def test_timeout_path_reports_and_recovers(S, monkeypatch, qs):
+    """Every wait of the tensor-core kernels is bounded by the global timer.
+    With the host-side hook the MMAs are never issued: the waits for them
+    (and, in the pipeline, every role's wait behind them) run out after 1 ms,
+    the kernel waits for its copies in flight, releases its tensor memory and
+    sets the error word; the next synchronising call reports SV_ERR_TIMEOUT
+    and the context stays usable.  The three qubit sets reach the pipeline
+    with loader warps, the pipeline with tensor-map loads and the two-group
+    kernel."""
     n = 14
     s = S.StateVector(n, "c64")
     monkeypatch.setenv("SV_FAULT_INJECT", "tc_wait")
-    s.apply_fused([0, 1], np.eye(4))
+    s.apply_fused(qs, np.eye(1 << len(qs)))
     with pytest.raises(S.SVError) as e:
         s.sync()
     assert e.value.status == 5
