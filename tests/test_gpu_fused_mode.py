@@ -42,7 +42,7 @@ def test_random_circuit_c64(S, orc, n, depth, seed):
     s = S.StateVector(n, "c64")
     p = s.plan(c, "fused")
     names = {k for k, _ in p.launch_info()}
-    assert all(k.startswith("k_fused_tc<k=") for k in names)  # blocks of at most k qubits
+    assert all(k.startswith(("k_fused_tc<k=", "k_fused_tc_groups<k=")) for k in names)  # tensor-core blocks
     assert p.passes < len(c) / 3
     p.execute()
     check("c64", s.to_numpy(), orc.run(c))
