@@ -46,6 +46,21 @@ def test_random_states(S, orc, dtype, tol, n):
     assert np.max(np.abs(got - ref)) <= tol
 
 
+@pytest.mark.parametrize("n", [14, 15, 24])
+def test_persistent_tiles(S, orc, n):
+    """Complex64 passes over 2^13-amplitude tiles run persistent CTAs (two
+    per SM): n = 14 and 15 give some CTAs one tile and leave the rest idle,
+    n = 24 gives each CTA six or seven tiles (the next tile's copies issued
+    under the current one's arithmetic, FP32 chunks of 8 tiles summed in
+    FP64)."""
+    psi = C.random_state(n, 90 + n)
+    s = S.StateVector(n, "c64")
+    s.from_numpy(psi)
+    got = s.expect_pauli()
+    ref = oracle_expect(orc, s.to_numpy().astype(np.complex128))
+    assert np.max(np.abs(got - ref)) <= 4e-6
+
+
 @pytest.mark.parametrize("low", ["4", "5", "8"])
 def test_low_qubit_variants(S, orc, monkeypatch, low):
     """Later passes that keep 4, 5 or 8 low qubits (SV_EXPECT_LOW) instead of
