@@ -26,8 +26,8 @@
 // qubits (every k = 6 block without qubit 0, or with qubits 0..3):
 //   loads: tensor-map copies (cp.async.bulk.tensor, 128-byte swizzle) by one
 //     thread, counted in bytes on the slot's mbarrier, when the columns run
-//     along the low qubits (form 0: the split's lanes along qubits 0..4 then
-//     meet no bank conflicts in the swizzled rows); otherwise 3 loader warps
+//     along the low qubits (form 0: the split's lanes along the columns then
+//     meet few bank conflicts in the swizzled rows); otherwise 3 loader warps
 //     with 16-byte cp.async (the slot's mbarrier counts each loader thread
 //     once its copies have landed: cp.async.mbarrier.arrive);
 //   converter warps (8): BF16 hi / lo split of a slot into one of two B
@@ -38,9 +38,10 @@
 //   epilogue warps (4, one per 32 tensor-memory lanes): tcgen05.ld of the
 //     accumulator, re / im of each amplitude joined by one shuffle, then to
 //     HBM: through a padded per-warp buffer, half the columns at a time,
-//     each store instruction writing whole rows (form 0: columns 0..7 are
-//     qubits 0..2), or straight from the registers, 8 bytes per lane (form
-//     1: each warp's 16 rows are qubits 0..3).
+//     each store instruction writing rows of 16 columns (form 0: columns
+//     0..3 are qubits 0..1, so at least whole 32-byte sectors), or straight
+//     from the registers, 8 bytes per lane (form 1: each warp's 16 rows are
+//     qubits 0..3).
 // In steady state the loads of the next tiles, the split of one, the MMAs
 // of another and the epilogue of a third run at once.
 //
@@ -910,11 +911,14 @@ void tc_prepare(int n, int k, const int *qubits, const double *U, uint16_t *a_op
     a.ntiles = uint64_t(1) << (n - kTcM);
     a.timeout_ns = 2000000000LL;
     // kernel and epilogue form: tile bits 0..3 are state qubits 0..3, so
-    // "columns 0..7 are qubits 0..2" means offN[c] = c, and "each epilogue
+    // "columns 0..3 are qubits 0..1" means offN[c] = c, and "each epilogue
     // warp's 16 rows are qubits 0..3" means the row amplitudes' tile bits
-    // 0..3 count 0..15; with neither, the two-group kernel (epi_mode 2)
+    // 0..3 count 0..15; with neither, the two-group kernel (epi_mode 2).
+    // (Columns 0..7 along qubits 0..2 was the first rule; 0..3 moved three
+    // of the 64 blocks of the 32-qubit benchmark's fused plan off the
+    // two-group kernel, 270 against about 275 us per 26-qubit launch.)
     bool cols = true, rows = true;
-    for (int c = 0; c < 8; ++c) cols = cols && a.offN[c] == c;
+    for (int c = 0; c < 4; ++c) cols = cols && a.offN[c] == c;
     for (int w = 0; w < 4 && rows; ++w)
         for (int r = 0; r < 16; ++r) {
             const int row = 32 * w + 2 * r;

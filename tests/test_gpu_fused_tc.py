@@ -88,7 +88,8 @@ def test_blocks_one_and_many_tiles(S, orc, n):
 # layout): the pipeline with loader warps and rows along the low qubits, the
 # pipeline with loader warps and columns along them (too many qubit runs for
 # the tensor map's five dimensions), the pipeline with tensor-map loads (one
-# box per tile; four boxes when two runs are iterated), and the two-group
+# box per tile; four boxes when two runs are iterated; columns along qubits
+# 0..1 only), and the two-group
 # kernel (qubit 0 among far-apart qubits, k < 6 with far-apart qubits).
 FORMS = [
     (22, [0, 1, 2, 3, 4, 5]),
@@ -98,6 +99,7 @@ FORMS = [
     (20, [14, 15, 16, 17, 18, 19]),
     (13, [7, 8, 9, 10, 11, 12]),
     (22, [3, 9, 12, 15, 18, 21]),
+    (22, [2, 3, 11, 12, 17, 18]),
     (14, [0, 9]),
     (22, [0, 7, 12, 13, 20, 21]),
     (22, [19, 20, 21]),
