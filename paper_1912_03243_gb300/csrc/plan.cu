@@ -151,10 +151,18 @@ sv_status upload_tile_plan(sv_plan_s *p, const TilePlan<R> &tp) {
     return SV_OK;
 }
 
-sv_status build_tile_plan(sv_state *h, const Circuit &c, sv_plan_s *p, const TileConfig &cfg) {
+sv_status build_tile_plan(sv_state *h, const Circuit &c, sv_plan_s *p, const TileConfig &cfg,
+                          const std::vector<int> &pass_ctas = std::vector<int>()) {
     if (h->dt == SV_C64) {
         TilePlan<float> tp;
         sv_status s = plan_tiles<float>(c, h->n, cfg, &tp);
+        if (!s && !pass_ctas.empty()) {
+            if (pass_ctas.size() != tp.passes.size()) {
+                set_error("per-pass CTA counts for %zu passes, the plan has %zu", pass_ctas.size(), tp.passes.size());
+                return SV_ERR_ARG;
+            }
+            tp.pass_ctas = pass_ctas;
+        }
         return s ? s : upload_tile_plan(p, tp);
     }
     TilePlan<double> tp;
@@ -219,17 +227,32 @@ std::string tile_cache_key(const sv_state *h, const TileConfig &cfg, const char 
 }
 
 // One candidate execution strategy: a mode, and for the tiled mode the tile
-// configuration, for the fused mode the block width (0 = fewest blocks).
+// configuration (and, optionally, the CTAs per SM of each pass), for the
+// fused mode the block width (0 = fewest blocks).
 struct Strategy {
     int mode = SV_MODE_TILED;
     TileConfig cfg{};
     int k = 0;
+    std::vector<int> pass_ctas;
     std::string name() const {
-        if (mode == SV_MODE_TILED) return "tiled " + tile_config_name(cfg);
+        if (mode == SV_MODE_TILED) {
+            std::string nm = "tiled " + tile_config_name(cfg);
+            if (!pass_ctas.empty()) {
+                nm += ",pass_ctas=";
+                for (int v : pass_ctas) nm += char('0' + v);
+            }
+            return nm;
+        }
         if (mode == SV_MODE_FUSED) return "fused k=" + std::to_string(k);
         return "pergate";
     }
 };
+
+std::string pass_ctas_key(const std::vector<int> &pc) {
+    std::string k;
+    for (int v : pc) k += char('0' + v);
+    return k;
+}
 
 TileConfig default_config(const sv_state *h) { return h->dt == SV_C64 ? tile_config64() : tile_config128(); }
 
@@ -240,7 +263,7 @@ sv_status create_plan(sv_state *h, const char *text, const Circuit &c, const Str
     const bool tiled = st.mode == SV_MODE_TILED && h->n >= tile_m;
     std::string key;
     if (tiled && text) {
-        key = tile_cache_key(h, st.cfg, text);
+        key = tile_cache_key(h, st.cfg, text) + "|" + pass_ctas_key(st.pass_ctas);
         std::lock_guard<std::mutex> lock(g_tile_cache_mu);
         auto it = g_tile_cache.find(key);
         if (it != g_tile_cache.end()) {
@@ -282,7 +305,7 @@ sv_status create_plan(sv_state *h, const char *text, const Circuit &c, const Str
                 p->bytes += b;
             }
     } else {
-        s = build_tile_plan(h, c, p, st.cfg);
+        s = build_tile_plan(h, c, p, st.cfg, st.pass_ctas);
         if (!s && !key.empty()) {
             std::lock_guard<std::mutex> lock(g_tile_cache_mu);
             if (g_tile_cache.size() >= kTileCacheMax) g_tile_cache.clear();
@@ -395,8 +418,12 @@ void tune_store(const std::string &key, const std::string &choice) {
 sv_status execute_direct(sv_plan_s *p);
 
 // Time each candidate on a scratch state; returns the index of the fastest
-// and a JSON report of all of them in *report.
-sv_status time_candidates(sv_state *h, const char *text, const Circuit &c, const std::vector<Strategy> &cand,
+// and a JSON report of all of them in *report.  Tiled candidates are also
+// timed pass by pass; where two of them differ only in the CTAs per SM their
+// passes are compiled for, a further candidate takes each pass in its faster
+// form (the pass plan does not depend on that count) and is appended to cand
+// and timed like the others.
+sv_status time_candidates(sv_state *h, const char *text, const Circuit &c, std::vector<Strategy> &cand,
                           size_t *best, std::string *report) {
     size_t free_b = 0, total_b = 0;
     SV_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
@@ -418,6 +445,8 @@ sv_status time_candidates(sv_state *h, const char *text, const Circuit &c, const
         if (cudaEventCreate(&ev[i]) != cudaSuccess) s = SV_ERR_CUDA;
     std::string js = "{\"timed\": true, \"candidates\": [";
     double best_ms = -1.0;
+    std::vector<std::vector<double>> pass_ms(cand.size());  // per launch, tiled candidates
+    bool mixed_added = false;
     for (size_t i = 0; i < cand.size() && s == SV_OK; ++i) {
         sv_plan_s *p = nullptr;
         sv_status cs = create_plan(&scratch, text, c, cand[i], &p);
@@ -432,10 +461,30 @@ sv_status time_candidates(sv_state *h, const char *text, const Circuit &c, const
             if (!cs) cs = sync_stream(scratch.stream, "autotune");
             float t = 0.0f;
             if (!cs && cudaEventElapsedTime(&t, ev[0], ev[1]) == cudaSuccess) ms = double(t) / reps;
+            // pass by pass (tiled plans): one more execution, an event between launches
+            const size_t nl = p->launches.size();
+            if (!cs && cand[i].mode == SV_MODE_TILED && cand[i].pass_ctas.empty() && nl > 0 &&
+                p->launches[0].kind == 1) {
+                std::vector<cudaEvent_t> pe(nl + 1, nullptr);
+                bool ok = true;
+                for (auto &e : pe) ok = ok && cudaEventCreate(&e) == cudaSuccess;
+                if (ok) cs = sv_plan_execute_timed(p, reinterpret_cast<void *const *>(pe.data()), int64_t(nl + 1));
+                if (ok && !cs) cs = sync_stream(scratch.stream, "autotune");
+                if (ok && !cs) {
+                    pass_ms[i].resize(nl);
+                    for (size_t j = 0; j < nl; ++j) {
+                        float tj = 0.0f;
+                        cudaEventElapsedTime(&tj, pe[j], pe[j + 1]);
+                        pass_ms[i][j] = double(tj);
+                    }
+                }
+                for (auto &e : pe)
+                    if (e) cudaEventDestroy(e);
+            }
             destroy_plan(p);
         }
         if (cs == SV_ERR_CUDA || cs == SV_ERR_TIMEOUT) s = cs;  // a device fault ends the tuning
-        char b[256];
+        char b[320];
         std::snprintf(b, sizeof b, "%s{\"strategy\": \"%s\", \"ms\": %.4f%s}", i ? ", " : "",
                       cand[i].name().c_str(), ms, cs ? ", \"failed\": true" : "");
         js += b;
@@ -443,8 +492,28 @@ sv_status time_candidates(sv_state *h, const char *text, const Circuit &c, const
             best_ms = ms;
             *best = i;
         }
-    }
-    for (cudaEvent_t e : ev)
+        // after the last original candidate: the per-pass mix of two that differ only in CTAs
+        if (i + 1 == cand.size() && !mixed_added && s == SV_OK) {
+            mixed_added = true;
+            for (size_t a2 = 0; a2 < i + 1; ++a2)
+                for (size_t a3 = 0; a3 < i + 1; ++a3) {
+                    const TileConfig &x = cand[a2].cfg, &y = cand[a3].cfg;
+                    if (a2 == a3 || pass_ms[a2].empty() || pass_ms[a2].size() != pass_ms[a3].size() ||
+                        x.ctas >= y.ctas || x.m != y.m || x.rb != y.rb || x.low != y.low || x.direct != y.direct ||
+                        x.prefetch != y.prefetch || x.c64 != y.c64)
+                        continue;
+                    Strategy mix = cand[a2];
+                    bool both = false, any = false;
+                    for (size_t j = 0; j < pass_ms[a2].size(); ++j) {
+                        const bool hi = pass_ms[a3][j] < pass_ms[a2][j];
+                        mix.pass_ctas.push_back(hi ? y.ctas : x.ctas);
+                        any = any || hi;
+                        both = both || !hi;
+                    }
+                    if (any && both && cand.size() < 64) cand.push_back(mix);
+                }
+        }
+    }    for (cudaEvent_t e : ev)
         if (e) cudaEventDestroy(e);
     cudaStreamSynchronize(scratch.stream);
     for (void *d : {static_cast<void *>(scratch.data), static_cast<void *>(scratch.d_partials),
@@ -463,15 +532,23 @@ sv_status time_candidates(sv_state *h, const char *text, const Circuit &c, const
 }
 
 sv_status create_auto_plan(sv_state *h, const char *text, const Circuit &c, sv_plan_s **out) {
-    const std::vector<Strategy> cand = candidates(h);
+    std::vector<Strategy> cand = candidates(h);
     const std::string key = tune_key(h, text);
     const std::string known = tune_lookup(key);
-    for (const Strategy &st : cand)
+    // a remembered per-pass mix: its base candidate's name, then ",pass_ctas=" and one digit per pass
+    const size_t mixed_at = known.find(",pass_ctas=");
+    for (const Strategy &base : cand) {
+        Strategy st = base;
+        if (mixed_at != std::string::npos) {
+            if (base.name() != known.substr(0, mixed_at)) continue;
+            for (size_t j = mixed_at + 11; j < known.size(); ++j) st.pass_ctas.push_back(known[j] - '0');
+        }
         if (!known.empty() && st.name() == known) {
             sv_status s = create_plan(h, text, c, st, out);
             if (!s) (*out)->tuning = "{\"timed\": false, \"remembered\": true, \"chosen\": \"" + known + "\"}";
             return s;
         }
+    }
     if (cand.size() == 1) {  // nothing to choose between (the two-byte code)
         sv_status s = create_plan(h, text, c, cand[0], out);
         if (!s)

@@ -110,6 +110,7 @@ struct TilePlan {
     // (2 per structured butterfly, 1 per T-type phase, 4 per other complex
     // phase or 8 per dense 2x2, times the fraction of amplitudes a control
     // or condition leaves; sign flips and X are free), and its segments
+    std::vector<int> pass_ctas;     // CTAs per SM each pass is compiled for (empty: ctas for all)
     std::vector<double> lane_ops;
     std::vector<int> nseg;
 };

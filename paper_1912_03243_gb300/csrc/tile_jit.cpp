@@ -190,7 +190,8 @@ std::string gen_pass(const TilePlan<R> &tp, size_t pass) {
     };
     int tpos[kTileMaxQ];
     for (int k = 0; k < tbits; ++k) tpos[k] = pa.tile_pos[k + G.EPC_LOG];
-    o << "extern \"C\" __global__ void __launch_bounds__(" << G.NT << ", " << tp.ctas << ") svp(" << C2T
+    const int ctas = tp.pass_ctas.empty() ? tp.ctas : tp.pass_ctas[pass];
+    o << "extern \"C\" __global__ void __launch_bounds__(" << G.NT << ", " << ctas << ") svp(" << C2T
       << "* __restrict__ psi, const u64 prm, const u64 ntiles) {\n";
     o << "  extern __shared__ __align__(16) unsigned char smem[];\n";
     o << "  " << C2T << "* sm = reinterpret_cast<" << C2T << "*>(smem);\n";
@@ -976,7 +977,9 @@ sv_status jit_plan_impl(const TilePlan<R> &tp, std::vector<void *> *fns) {
             if (ce != cudaSuccess) return cuda_status(ce, "loading a compiled pass");
             it = g_jit.emplace(key[size_t(j)], e).first;
             g_jit_smem[reinterpret_cast<const void *>(e.fn)] =
-                PassLaunch{smem, hbm_io(tp, size_t(j)).prefetch ? tp.ctas : 0, tp.m};
+                PassLaunch{smem,
+                           hbm_io(tp, size_t(j)).prefetch ? (tp.pass_ctas.empty() ? tp.ctas : tp.pass_ctas[size_t(j)]) : 0,
+                           tp.m};
         }
         (*fns)[size_t(j)] = reinterpret_cast<void *>(it->second.fn);
     }
