@@ -485,7 +485,7 @@ sv_status time_candidates(sv_state *h, const char *text, const Circuit &c, std::
         }
         if (cs == SV_ERR_CUDA || cs == SV_ERR_TIMEOUT) s = cs;  // a device fault ends the tuning
         char b[320];
-        std::snprintf(b, sizeof b, "%s{\"strategy\": \"%s\", \"ms\": %.4f%s}", i ? ", " : "",
+        std::snprintf(b, sizeof b, "%s{\"strategy\": \"%s\", \"ms\": %.6f%s}", i ? ", " : "",
                       cand[i].name().c_str(), ms, cs ? ", \"failed\": true" : "");
         js += b;
         if (ms > 0 && (best_ms < 0 || ms < best_ms)) {

@@ -42,7 +42,8 @@ def test_tuned_plan_matches_the_oracle(S, orc, fresh_tuning, n, dtype, tol):
     assert rep["chosen"] in names
     assert all(x["ms"] > 0 for x in rep["candidates"] if not x.get("failed"))
     best = min((x for x in rep["candidates"] if x["ms"] > 0), key=lambda x: x["ms"])
-    assert rep["chosen"] == best["strategy"]
+    chosen_ms = next(x["ms"] for x in rep["candidates"] if x["strategy"] == rep["chosen"])
+    assert chosen_ms <= best["ms"] + 2e-6  # the fastest (ties within the report's rounding aside)
     if n >= 13:
         assert any(nm.startswith("tiled") for nm in names)
     assert any(nm.startswith("fused k=6") for nm in names)
