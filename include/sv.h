@@ -220,6 +220,26 @@ sv_status sv_plan_pass_source(const char *text, int n, sv_dtype dt, int64_t pass
 sv_status sv_plan_stats(const char *text, int n, sv_dtype dt, int compile, int64_t *gates, int64_t *passes,
                         int64_t *segments);
 
+/* Host only (no GPU needed): which tensor-core kernel a dense k-qubit block
+ * on these qubits of an n-qubit complex64 state runs (Sec. 2: the block acts
+ * on the amplitudes that differ only in its qubits; the library's kernel for
+ * it is chosen from the qubit layout) and, when it loads its tiles with
+ * tensor-map copies, the map's layout: the tile's 12 qubits (tile_pos, bit t
+ * of a tile index is state qubit tile_pos[t]); tma_rank dimensions, where
+ * dimension d holds the qubits from tma_start[d] up to the next start (the
+ * last up to n), of size dim[d], byte stride stride[d - 1] for d >= 1 (8-byte
+ * elements), box[d] elements copied; tma_nbox boxes per tile at global
+ * element offsets tma_boff[b] from the tile's base, laid out one after the
+ * other in shared memory.  Without tensor-map loads tma_rank = tma_nbox = 0
+ * and the map fields are 0.  kernel (cap bytes, NUL-terminated, may be NULL)
+ * receives the launch name (k_fused_tc<k=..>, k_fused_tc<k=..,tma> or
+ * k_fused_tc_groups<k=..>); every other output may be NULL (arrays: 12, 5,
+ * 4, 5, 4 and 5 entries).  Errors: SV_ERR_ARG (n outside 12..40, k outside
+ * 1..6, repeated or out-of-range qubits). */
+sv_status sv_fused_tc_layout(int n, int k, const int *qubits, char *kernel, size_t cap, int *tile_pos,
+                             int *tma_rank, int *tma_nbox, int *tma_start, uint64_t *tma_boff, uint64_t *dim,
+                             uint64_t *stride, uint32_t *box);
+
 /* ---- batches of independent circuits ------------------------------------------ */
 
 /* A batch of count independent circuits, member k = texts[k] on its own

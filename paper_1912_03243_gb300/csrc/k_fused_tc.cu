@@ -985,19 +985,15 @@ EncodeTiledFn encode_tiled_fn() {
 // qubits TcArgs::tma_start sets out (sizes 2^range, strides the products of
 // the ones below: the plain layout), padded to five dimensions of size 1; the
 // box covers the tile's part of each range; 128-byte swizzle.
-cudaError_t encode_tile_map(void *data, int n, const TcArgs &a, CUtensorMap *map) {
-    const EncodeTiledFn fn = encode_tiled_fn();
-    if (!fn) return cudaErrorNotSupported;
-    cuuint64_t dim[5], stride[4];
-    cuuint32_t box[5], estr[5] = {1, 1, 1, 1, 1};
+void tile_map_dims(int n, const TcArgs &a, uint64_t dim[5], uint64_t stride[4], uint32_t box[5]) {
     uint64_t bytes = 8;  // stride of the current dimension
     for (int d = 0; d < 5; ++d) {
         if (d < a.tma_rank) {
             const int lo = a.tma_start[d], hi = d + 1 < a.tma_rank ? a.tma_start[d + 1] : n;
-            dim[d] = cuuint64_t(1) << (hi - lo);
+            dim[d] = uint64_t(1) << (hi - lo);
             int in_tile = 0;  // tile qubits in [lo, hi): qubits 0..3, the rest of run 0, or a run (and iterated ones)
             for (int t = 0; t < kTcM; ++t) in_tile += a.tile_pos[t] >= lo && a.tile_pos[t] < hi;
-            box[d] = cuuint32_t(1) << in_tile;
+            box[d] = uint32_t(1) << in_tile;
         } else {
             dim[d] = 1;
             box[d] = 1;
@@ -1006,12 +1002,25 @@ cudaError_t encode_tile_map(void *data, int n, const TcArgs &a, CUtensorMap *map
         bytes *= dim[d];
     }
     // iterated runs lie inside the last range but outside the box
-    {
-        int it = 0;
-        for (int b = a.tma_nbox; b > 1; b >>= 1) ++it;
-        box[a.tma_rank - 1] >>= it;
+    int it = 0;
+    for (int b = a.tma_nbox; b > 1; b >>= 1) ++it;
+    box[a.tma_rank - 1] >>= it;
+}
+
+cudaError_t encode_tile_map(void *data, int n, const TcArgs &a, CUtensorMap *map) {
+    const EncodeTiledFn fn = encode_tiled_fn();
+    if (!fn) return cudaErrorNotSupported;
+    uint64_t dim[5], stride[4];
+    uint32_t box[5];
+    tile_map_dims(n, a, dim, stride, box);
+    cuuint64_t cdim[5], cstride[4];
+    cuuint32_t cbox[5], estr[5] = {1, 1, 1, 1, 1};
+    for (int d = 0; d < 5; ++d) {
+        cdim[d] = dim[d];
+        cbox[d] = box[d];
+        if (d < 4) cstride[d] = stride[d];
     }
-    const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 5, data, dim, stride, box, estr,
+    const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 5, data, cdim, cstride, cbox, estr,
                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
@@ -1090,3 +1099,47 @@ cudaError_t launch_fused_tc(sv_state *h, int k, const int *qubits, const double 
 }
 
 }  // namespace sv
+
+using namespace sv;
+
+extern "C" sv_status sv_fused_tc_layout(int n, int k, const int *qubits, char *kernel, size_t cap, int *tile_pos,
+                                        int *tma_rank, int *tma_nbox, int *tma_start, uint64_t *tma_boff,
+                                        uint64_t *dim, uint64_t *stride, uint32_t *box) {
+    if (n < kTcM || n > kMaxQubits || k < 1 || k > 6 || !qubits) {
+        set_error("need 12 <= n <= %d, 1 <= k <= 6 and the block's qubits", kMaxQubits);
+        return SV_ERR_ARG;
+    }
+    for (int j = 0; j < k; ++j) {
+        bool dup = false;
+        for (int i = 0; i < j; ++i) dup = dup || qubits[i] == qubits[j];
+        if (qubits[j] < 0 || qubits[j] >= n || dup) {
+            set_error("block qubits must be distinct and in [0, n)");
+            return SV_ERR_ARG;
+        }
+    }
+    std::vector<double> U(size_t(2) << (2 * k), 0.0);
+    for (int i = 0; i < (1 << k); ++i) U[size_t(2) * (size_t(i) * (size_t(1) << k) + size_t(i))] = 1.0;
+    std::vector<uint16_t> img(2 * 128 * 128);
+    TcArgs a;
+    tc_prepare(n, k, qubits, U.data(), img.data(), &a);
+    const char *nm = tc_kernel_name(a);
+    if (kernel && cap) {
+        std::strncpy(kernel, nm, cap - 1);
+        kernel[cap - 1] = '\0';
+    }
+    if (tile_pos)
+        for (int t = 0; t < kTcM; ++t) tile_pos[t] = a.tile_pos[t];
+    if (tma_rank) *tma_rank = a.tma ? a.tma_rank : 0;
+    if (tma_nbox) *tma_nbox = a.tma ? a.tma_nbox : 0;
+    uint64_t d5[5] = {0, 0, 0, 0, 0}, s4[4] = {0, 0, 0, 0};
+    uint32_t b5[5] = {0, 0, 0, 0, 0};
+    if (a.tma) tile_map_dims(n, a, d5, s4, b5);
+    for (int d = 0; d < 5; ++d) {
+        if (tma_start) tma_start[d] = a.tma && d < a.tma_rank ? a.tma_start[d] : 0;
+        if (dim) dim[d] = d5[d];
+        if (box) box[d] = b5[d];
+        if (stride && d < 4) stride[d] = s4[d];
+        if (tma_boff && d < 4) tma_boff[d] = a.tma && d < a.tma_nbox ? a.tma_boff[d] : 0;
+    }
+    return SV_OK;
+}

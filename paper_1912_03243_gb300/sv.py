@@ -58,6 +58,8 @@ SIGNATURES = {
     "sv_plan_tuning": (_st, [_vp, ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
     "sv_plan_pass_source": (_st, [ctypes.c_char_p, ctypes.c_int, ctypes.c_int, ctypes.c_int64, ctypes.c_char_p,
                                   ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
+    "sv_fused_tc_layout": (_st, [ctypes.c_int, ctypes.c_int, _ip, ctypes.c_char_p, ctypes.c_size_t, _ip, _ip, _ip,
+                                 _ip, _u64p, _u64p, _u64p, ctypes.POINTER(ctypes.c_uint32)]),
     "sv_encode2b": (_st, [_vp, _vp]),
     "sv_decode2b": (_st, [_vp, _vp]),
     "sv_get_codes": (_st, [_vp, ctypes.POINTER(ctypes.c_int8), ctypes.POINTER(ctypes.c_float)]),
@@ -167,6 +169,26 @@ def sv_plan_pass_source(circuit, n: int, dtype: str | int, pass_index: int) -> s
     _check(lib().sv_plan_pass_source(t, n, dt, pass_index, buf, ln.value + 1, ctypes.byref(ln)),
            "sv_plan_pass_source")
     return buf.value.decode()
+
+
+def sv_fused_tc_layout(n: int, qubits) -> dict:
+    """Host-only: the tensor-core kernel a dense block on these qubits runs
+    and its tensor-map layout (see include/sv.h)."""
+    qs = np.asarray(list(qubits), dtype=np.int32)
+    name = ctypes.create_string_buffer(64)
+    tpos = np.zeros(12, np.int32)
+    rank, nbox = ctypes.c_int(), ctypes.c_int()
+    start = np.zeros(5, np.int32)
+    boff, dim, stride = np.zeros(4, np.uint64), np.zeros(5, np.uint64), np.zeros(4, np.uint64)
+    box = np.zeros(5, np.uint32)
+    _check(lib().sv_fused_tc_layout(n, len(qs), qs.ctypes.data_as(_ip), name, 64, tpos.ctypes.data_as(_ip),
+                                    ctypes.byref(rank), ctypes.byref(nbox), start.ctypes.data_as(_ip),
+                                    boff.ctypes.data_as(_u64p), dim.ctypes.data_as(_u64p),
+                                    stride.ctypes.data_as(_u64p), box.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))),
+           "sv_fused_tc_layout")
+    return {"kernel": name.value.decode(), "tile_pos": tpos.tolist(), "rank": rank.value, "nbox": nbox.value,
+            "start": start.tolist(), "boff": [int(x) for x in boff], "dim": [int(x) for x in dim],
+            "stride": [int(x) for x in stride], "box": [int(x) for x in box]}
 
 
 def tiled_pass_sources(case: str) -> str:
